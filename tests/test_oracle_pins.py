@@ -1,0 +1,407 @@
+"""Pins for the FP64 CPU oracle: each test checks the oracle against something other than itself
+(dense solves, textbook MINRES, an explicitly formed block Krylov basis, exact structural facts
+printed in the paper, closed forms), so that a dropped term, a wrong sign or index, or a
+transposed operand in the oracle fails at least one of them."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------------------------
+# independent references written here from textbook definitions
+# ---------------------------------------------------------------------------------------------
+
+def minres_textbook(A, b, x0=None, maxit=100, tol=0.0):
+    """Single-vector MINRES (Paige & Saunders 1975): symmetric Lanczos + Givens QR of the
+    tridiagonal matrix, three-term direction recurrence.  Returns iterates and |eta_k|."""
+    n = A.shape[0]
+    x = np.zeros(n) if x0 is None else x0.astype(float).copy()
+    r0 = b - A @ x
+    beta1 = np.linalg.norm(r0)
+    xs, res = [], []
+    if beta1 == 0:
+        return xs, res
+    v_prev = np.zeros(n)
+    v = r0 / beta1
+    beta_k = 0.0  # T entry above the diagonal in the current column
+    c2, s2 = 1.0, 0.0  # rotation k-2
+    c1, s1 = 1.0, 0.0  # rotation k-1
+    w2 = np.zeros(n)
+    w1 = np.zeros(n)
+    eta = beta1
+    for _ in range(maxit):
+        Av = A @ v
+        alpha = v @ Av
+        vn = Av - alpha * v - beta_k * v_prev
+        beta_next = np.linalg.norm(vn)
+        # previous rotations applied to column k = (beta_k, alpha, beta_next) in rows k-1, k, k+1
+        eps = s2 * beta_k
+        d1 = c2 * beta_k
+        delta = c1 * d1 + s1 * alpha
+        g1 = -s1 * d1 + c1 * alpha
+        gam = math.hypot(g1, beta_next)
+        c, s = g1 / gam, beta_next / gam
+        w = (v - eps * w2 - delta * w1) / gam
+        x = x + c * eta * w
+        eta = -s * eta
+        xs.append(x.copy())
+        res.append(abs(eta))
+        if abs(eta) < tol * beta1:
+            break
+        w2, w1 = w1, w
+        c2, s2, c1, s1 = c1, s1, c, s
+        v_prev, v = v, (vn / beta_next if beta_next > 0 else vn)
+        beta_k = beta_next
+    return xs, res
+
+
+def band_krylov_basis(A, F0, j):
+    """Orthonormal basis of the first j vectors of f_1..f_p, A f_1..A f_p, A^2 f_1, ...
+    (the band Krylov sequence), built with full re-orthogonalisation (two passes)."""
+    n, p = F0.shape
+    Q = []
+    for t in range(j):
+        if t < p:
+            v = F0[:, t].copy()
+        else:
+            v = A @ Q[t - p]
+        for _ in range(2):
+            for q in Q:
+                v -= (q @ v) * q
+        Q.append(v / np.linalg.norm(v))
+    return np.stack(Q, axis=1)
+
+
+def read_pattern(name):
+    lines = [ln.strip() for ln in open(os.path.join(GOLDEN, name)) if ln.strip() and not ln.startswith("#")]
+    meta, mats, cur = {}, {}, None
+    for ln in lines:
+        tok = ln.split()
+        if tok[0] in ("H", "R"):
+            cur = tok[0]
+            mats[cur] = []
+        elif cur is None:
+            meta[tok[0]] = tok[1]
+        else:
+            mats[cur].append(tok)
+    return meta, mats
+
+
+# ---------------------------------------------------------------------------------------------
+
+def test_bench_generator_properties(oracle_mod):
+    v = oracle_mod.bench_values(7, 0, 100000, range(100000))
+    assert np.all(v >= -1.0) and np.all(v < 1.0)
+    assert abs(v.mean()) < 0.01 and abs(v.var() - 1.0 / 3.0) < 0.01
+    # counter based: entry (k, row) depends only on (seed, k*n + row)
+    a = oracle_mod.bench_values(7, 1, 50, [3, 4])
+    b = oracle_mod.bench_values(7, 0, 50, [53, 54])
+    assert np.array_equal(a, b)
+    assert not np.array_equal(oracle_mod.bench_values(8, 0, 50, [3]), oracle_mod.bench_values(7, 0, 50, [3]))
+    # 53-bit values: v + 1 is a multiple of 2^-52
+    assert np.all(np.mod((v[:1000] + 1.0) * 2.0**52, 1.0) == 0.0)
+
+
+@pytest.mark.parametrize("n,p,seed", [(8, 1, 0), (30, 2, 1), (60, 3, 2), (120, 5, 3), (40, 4, 4)])
+def test_P1_dense_lu(oracle_mod, workloads, n, p, seed):
+    """Run to convergence on small random symmetric indefinite systems; compare with LU."""
+    A = workloads.random_symmetric_indefinite(n, seed)
+    B = workloads.randn_rhs(n, p, seed + 10)
+    r = oracle_mod.bminres(A, B, tol=1e-13, maxit=20 * n)
+    assert r.status == 0, r.status_name
+    D = A.to_dense()
+    X = np.linalg.solve(D, B)
+    kappa = np.linalg.cond(D)
+    assert np.linalg.norm(r.X - X) / np.linalg.norm(X) <= kappa * 1e-11
+    assert np.all(oracle_mod.relres(A, B, r.X) < 1e-10)
+
+
+def test_P1_nonzero_initial_guess(oracle_mod, workloads):
+    A = workloads.random_symmetric_indefinite(50, 5)
+    B = workloads.randn_rhs(50, 3, 6)
+    X0 = workloads.randn_rhs(50, 3, 7)
+    r = oracle_mod.bminres(A, B, X0=X0, tol=1e-13, maxit=1000)
+    X = np.linalg.solve(A.to_dense(), B)
+    assert r.status == 0
+    assert np.linalg.norm(r.X - X) / np.linalg.norm(X) < 1e-10
+
+
+def test_P2_p1_is_classical_minres(oracle_mod, workloads):
+    """With p = 1 the band method is MINRES: every iterate and the iteration count agree."""
+    A = workloads.laplacian(12, 2, workloads.shift_at_fraction(12, 2, 0.3))
+    D = A.to_dense()
+    b = workloads.randn_rhs(A.n, 1, 3)
+    xs, res = minres_textbook(D, b[:, 0], maxit=2000, tol=1e-10)
+    r = oracle_mod.bminres(A, b, tol=1e-10, maxit=2000, hist=2000, xhist=60)
+    assert r.status == 0
+    # iterates agree until Ritz values converge; after that any two MINRES implementations
+    # (scipy's included) drift apart at rounding level amplified by the near-singular projected
+    # problem, so later steps are compared through the residual history and iteration count
+    for k in range(30):
+        ref = xs[k]
+        assert np.linalg.norm(r.Xhist[k][:, 0] - ref) <= 1e-10 * np.linalg.norm(ref), k
+    assert np.all(np.abs(r.rho[:40, 0] - np.array(res[:40])) <= 1e-10 * res[0])
+    assert abs(r.iters - len(xs)) <= 3
+
+
+def test_P2_scipy_minres_iterates(oracle_mod, workloads):
+    sla = pytest.importorskip("scipy.sparse.linalg")
+    A = workloads.laplacian(10, 2, workloads.shift_at_fraction(10, 2, 0.2))
+    b = workloads.randn_rhs(A.n, 1, 4)[:, 0]
+    its = []
+    sla.minres(A.to_scipy(), b, rtol=1e-30, maxiter=40, callback=lambda xk: its.append(xk.copy()))
+    r = oracle_mod.bminres(A, b[:, None], tol=1e-14, maxit=40, xhist=40)
+    for k in range(30):
+        assert np.linalg.norm(r.Xhist[k][:, 0] - its[k]) <= 1e-9 * np.linalg.norm(its[k])
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_P3_minimum_residual_property(oracle_mod, workloads, p):
+    """X_j column i minimises ||b_i - A x|| over x0_i + span(first j band Krylov vectors)."""
+    A = workloads.random_symmetric_indefinite(160, 11 + p)
+    D = A.to_dense()
+    B = workloads.randn_rhs(A.n, p, 21)
+    jmax = 5 * 3 * p
+    r = oracle_mod.bminres(A, B, tol=1e-15, maxit=jmax, hist=jmax, xhist=jmax)
+    assert r.iters == jmax
+    for j in range(1, jmax + 1):
+        Q = band_krylov_basis(D, B, j)
+        AQ = D @ Q
+        for i in range(p):
+            y, *_ = np.linalg.lstsq(AQ, B[:, i], rcond=None)
+            x = Q @ y
+            resid = np.linalg.norm(B[:, i] - AQ @ y)
+            assert abs(r.rho[j - 1, i] - resid) <= 1e-10 * np.linalg.norm(B[:, i]), (j, i)
+            assert np.linalg.norm(r.Xhist[j - 1][:, i] - x) <= 1e-9 * max(np.linalg.norm(x), 1e-300), (j, i)
+
+
+def test_P4_P5_monotone_and_recursive_equals_true(oracle_mod, workloads):
+    A = workloads.laplacian(14, 2, workloads.shift_at_fraction(14, 2, 0.15))
+    B = workloads.randn_rhs(A.n, 3, 2)
+    r = oracle_mod.bminres(A, B, tol=1e-11, maxit=3000, hist=3000, xhist=400)
+    assert r.status == 0
+    d = np.diff(r.rho, axis=0)
+    assert np.all(d <= 1e-13 * r.f0norm[None, :])  # recursive residual never increases
+    nb = np.linalg.norm(B, axis=0)
+    true = []
+    for k in range(r.Xhist.shape[0]):
+        R = B - oracle_mod.spmm(A, r.Xhist[k])
+        true.append(np.linalg.norm(R, axis=0))
+    true = np.array(true)
+    mask = r.rho[: len(true)] >= 1e-9 * nb
+    assert np.all(np.abs(r.rho[: len(true)] - true)[mask] <= 1e-11 * np.broadcast_to(nb, true.shape)[mask])
+    assert np.all(np.diff(true, axis=0) <= 1e-12 * nb)
+
+
+def test_P6_band_structure(oracle_mod, workloads):
+    """U_{j+p}^T A U_j equals the banded H-bar_j (p sub- and p superdiagonals)."""
+    p = 3
+    A = workloads.random_symmetric_indefinite(90, 31)
+    D = A.to_dense()
+    B = workloads.randn_rhs(90, p, 32)
+    J = 24
+    r = oracle_mod.bminres(A, B, tol=1e-15, maxit=J, hist=J, uhist=J + p)
+    U = r.U.T  # n x (J + p)
+    G = U.T @ D @ U[:, :J]  # (J+p) x J
+    Hbar = np.zeros((J + p, J))
+    for j in range(1, J + 1):
+        for t in range(2 * p + 1):
+            i = j - p + t
+            if 1 <= i <= J + p:
+                Hbar[i - 1, j - 1] = r.H[j - 1, t]
+    assert np.abs(G - Hbar).max() <= 1e-12 * np.abs(D).max()
+    # band: entries outside |i - j| <= p vanish; C_j (last p rows) is upper triangular
+    ii, jj = np.indices(G.shape)
+    assert np.abs(G[np.abs(ii - jj) > p]).max() <= 1e-12 * np.abs(D).max()
+    # symmetry of the square part H_j = U_j^T A U_j
+    assert np.allclose(Hbar[:J, :J], Hbar[:J, :J].T, atol=1e-12 * np.abs(D).max())
+
+
+def test_golden_c_queue_indexing(oracle_mod, workloads):
+    """Rows 2..6 of column 7 (p=5) are copies of entries computed at iterations 2..6 (Eq. (anti-diag-symmetry))."""
+    lines = [ln.split() for ln in open(os.path.join(GOLDEN, "c_queue_p5_j7.txt")) if ln.strip() and not ln.startswith("#")]
+    p = int([t for t in lines if t[0] == "p"][0][1])
+    j = int([t for t in lines if t[0] == "j"][0][1])
+    pairs = [t for t in lines if t[0].startswith("h_")]
+    A = workloads.random_symmetric_indefinite(80, 41)
+    B = workloads.randn_rhs(80, p, 42)
+    r = oracle_mod.bminres(A, B, tol=1e-15, maxit=12, hist=12)
+
+    def H(i, jj):  # entry (i, jj) of H-bar from the recorded bands (1-based)
+        return r.H[jj - 1, i - (jj - p)]
+
+    for t in pairs:
+        a = [int(s) for s in t[0].split("_")[1:]]
+        b = [int(s) for s in t[2].split("_")[1:]]
+        assert H(*a) == H(*b) and H(*a) != 0.0  # copied, not recomputed
+    assert j == 7
+
+
+def test_P7_substitution_structure_golden(oracle_mod, workloads):
+    """A forced dependence at iteration 5 with p = 2 reproduces the printed zero pattern."""
+    meta, mats = read_pattern("substitution_pattern_p2.txt")
+    p = int(meta["p"])
+    jdep = int(meta["dependent_iteration"])
+    n = 40
+    rng = np.random.default_rng(5)
+    Qm, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = rng.uniform(0.5, 4.0, n) * np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    D = (Qm * lam) @ Qm.T
+    D = 0.5 * (D + D.T)
+    A = workloads.dense_to_csr(D)
+    # f_1 lies in a 3-dimensional invariant subspace: A^3 f_1 depends on f_1, A f_1, A^2 f_1
+    f1 = Qm[:, :3] @ np.array([1.0, -0.7, 0.4])
+    B = np.stack([f1, rng.standard_normal(n)], axis=1)
+    for qr in ("householder", "givens"):
+        r = oracle_mod.bminres(A, B, tol=1e-15, maxit=10, hist=10, bench=2, qr=qr)
+        assert r.defl_iters[:1] == [jdep]
+        Hm = mats["H"]
+        Rm = mats["R"]
+        for jj in range(1, 11):
+            for t in range(2 * p + 1):
+                i = jj - p + t
+                if 1 <= i <= len(Hm):
+                    e = Hm[i - 1][jj - 1]
+                    v = r.H[jj - 1, t]
+                    if e == "0":
+                        assert v == 0.0, ("H", i, jj)
+                    elif e == "x":
+                        assert v != 0.0, ("H", i, jj)
+                i = jj - 2 * p + t
+                if 1 <= i <= len(Rm):
+                    e = Rm[i - 1][jj - 1]
+                    v = r.R[jj - 1, t]
+                    if e == "0":
+                        assert v == 0.0, ("R", i, jj, qr)
+                    elif e == "x":
+                        assert v != 0.0, ("R", i, jj, qr)
+
+
+def test_P8_dependence_demo(oracle_mod, workloads):
+    """B = [e_1, A e_1]: dependence at iteration 1; column 2 is solved exactly by e_1."""
+    meta = dict(ln.split()[:2] for ln in open(os.path.join(GOLDEN, "dependence_demo_e3.txt")) if ln.strip() and not ln.startswith("#"))
+    N = 20
+    A = workloads.laplacian(N, 2, workloads.shift_at_fraction(N, 2, 0.3))
+    e1 = np.zeros(A.n)
+    e1[0] = 1.0
+    B = np.stack([e1, oracle_mod.spmm(A, e1[:, None])[:, 0]], axis=1)
+    r = oracle_mod.bminres(A, B, tol=1e-10, maxit=4000, hist=4000, xhist=3)
+    assert r.status == 0
+    assert r.defl_iters[0] == int(meta["dependent_iteration"])
+    j = int(meta["column_2_converged_at_iteration"])
+    assert r.rho[j - 1, 1] <= 1e-14 * r.f0norm[1]
+    assert np.linalg.norm(r.Xhist[j - 1][:, 1] - e1) <= 1e-14
+    assert np.linalg.norm(r.X[:, 1] - e1) <= 1e-12
+    assert oracle_mod.relres(A, B, r.X)[0] < 1e-9
+
+
+def test_P9_convergence_bound_vs_single_minres(oracle_mod, workloads):
+    """Column i after j band iterations is no worse than MINRES on b_i alone after
+    J_i = floor((j - i)/p) + 1 steps (Sec. 6; K_J(A, f_i) lies in the span of U_j)."""
+    p = 3
+    A = workloads.laplacian(16, 2, workloads.shift_at_fraction(16, 2, 0.2))
+    D = A.to_dense()
+    B = workloads.randn_rhs(A.n, p, 8)
+    jmax = 60
+    r = oracle_mod.bminres(A, B, tol=1e-15, maxit=jmax, hist=jmax)
+    for i in range(1, p + 1):
+        _, res = minres_textbook(D, B[:, i - 1], maxit=jmax)
+        res = [np.linalg.norm(B[:, i - 1])] + res
+        for j in range(i, jmax + 1):
+            J = (j - i) // p + 1
+            assert r.rho[j - 1, i - 1] <= res[J] * (1 + 1e-9) + 1e-13 * res[0], (i, j, J)
+
+
+def test_P10_config1_singular_and_projected(oracle_mod, workloads):
+    A, B = workloads.config_c1()
+    Q = workloads.laplacian_null_modes_2d(32, 4.0)
+    assert Q.shape[1] == 32
+    D = A.to_dense()
+    assert np.abs(D @ Q).max() < 1e-13
+    floor = np.linalg.norm(Q.T @ B, axis=0) / np.linalg.norm(B, axis=0)
+    lit = oracle_mod.bminres(A, B, tol=1e-10, maxit=2000, hist=2000)
+    assert lit.status == 1  # cannot reach 1e-10
+    est = lit.rho[-1] / lit.f0norm
+    assert np.all(np.abs(est - floor) <= 1e-3 * floor)
+    # the true residual of the iterate cannot beat the least-squares floor; with A singular and B
+    # not in its range, X picks up large null-space-adjacent components, so rounding keeps the true
+    # residual a little above the recursive one
+    true = oracle_mod.relres(A, B, lit.X)
+    assert np.all(true >= floor * (1 - 1e-12)) and np.all(true <= 1.02 * floor)
+    Bp = workloads.project_out(B, Q)
+    pr = oracle_mod.bminres(A, Bp, tol=1e-10, maxit=4000)
+    assert pr.status == 0
+    assert np.all(oracle_mod.relres(A, Bp, pr.X) <= 2e-10)
+    w, V = np.linalg.eigh(D)
+    keep = np.abs(w) > 1e-10
+    Xp = V[:, keep] @ ((V[:, keep].T @ Bp) / w[keep, None])  # pseudo-inverse solution
+    Xr = pr.X - Q @ (Q.T @ pr.X)  # component in range(A)
+    kappa_eff = np.abs(w[keep]).max() / np.abs(w[keep]).min()
+    assert np.linalg.norm(Xr - Xp) / np.linalg.norm(Xp) <= kappa_eff * 1e-10
+
+
+def test_P11_local_orthogonality(oracle_mod, workloads):
+    p = 4
+    A = workloads.laplacian(12, 2, workloads.shift_at_fraction(12, 2, 0.25))
+    B = workloads.randn_rhs(A.n, p, 9)
+    r = oracle_mod.bminres(A, B, tol=1e-15, maxit=200, uhist=200 + p)
+    U = r.U
+    assert r.iters > 150
+    for j in range(1, r.iters + 1):
+        lo, hi = max(0, j - p - 1), j + p  # u_{j-p} .. u_{j+p}
+        G = U[lo:hi] @ U[lo:hi].T
+        assert np.abs(G - np.eye(hi - lo)).max() <= 1e-10, j
+    # global orthogonality early on (before Ritz values converge)
+    G = U[:40] @ U[:40].T
+    assert np.abs(G - np.eye(40)).max() <= 1e-10
+
+
+def test_P12_householder_givens_same_iterates(oracle_mod, workloads):
+    A = workloads.laplacian(10, 3, workloads.shift_at_fraction(10, 3, 0.1))
+    B = workloads.randn_rhs(A.n, 4, 3)
+    a = oracle_mod.bminres(A, B, tol=1e-10, maxit=3000, xhist=100, hist=3000)
+    g = oracle_mod.bminres(A, B, tol=1e-10, maxit=3000, xhist=100, hist=3000, qr="givens")
+    assert a.status == 0 and g.status == 0
+    for k in range(100):
+        assert np.linalg.norm(a.Xhist[k] - g.Xhist[k]) <= 1e-12 * np.linalg.norm(a.Xhist[k])
+    # R differs at most by row signs: |R| agrees
+    assert np.allclose(np.abs(a.R[:100]), np.abs(g.R[:100]), rtol=1e-10, atol=1e-12)
+    assert abs(a.iters - g.iters) <= 1
+
+
+def test_dependent_rhs_setup_deflation(oracle_mod, workloads):
+    """Config-2 structure on a small grid: columns 6 and 7 are dependent at set-up."""
+    A = workloads.laplacian(12, 3, workloads.shift_at_fraction(12, 3, 0.10))
+    B = workloads.dependent_rhs_p8(A.n, seed=0)
+    r = oracle_mod.bminres(A, B, tol=1e-10, maxit=20000, bench=4)
+    assert r.setup_deflations == 2 and r.bench_used >= 2
+    assert r.status == 0
+    assert np.all(oracle_mod.relres(A, B, r.X) < 2e-10)
+    X = np.linalg.solve(A.to_dense(), B)
+    kappa = np.linalg.cond(A.to_dense())
+    assert np.linalg.norm(r.X - X) / np.linalg.norm(X) <= kappa * 1e-10
+
+
+def test_zero_rhs_column_and_degenerate_sizes(oracle_mod, workloads):
+    A = workloads.laplacian(8, 2, workloads.shift_at_fraction(8, 2, 0.3))
+    B = workloads.randn_rhs(A.n, 3, 1)
+    B[:, 1] = 0.0
+    r = oracle_mod.bminres(A, B, tol=1e-10, maxit=2000)
+    assert r.status == 0 and r.setup_deflations == 1
+    assert np.all(r.X[:, 1] == 0.0)
+    X = np.linalg.solve(A.to_dense(), B)
+    assert np.linalg.norm(r.X - X) / np.linalg.norm(X) < 1e-8
+    # all-zero right-hand side: nothing to do
+    z = oracle_mod.bminres(A, np.zeros((A.n, 2)), tol=1e-10, maxit=10)
+    assert z.status == 0 and z.iters == 0
+    # p > n is rejected
+    A1 = workloads.laplacian(2, 1)
+    bad = oracle_mod.bminres(A1, np.ones((2, 3)), tol=1e-10, maxit=10)
+    assert bad.status == -1
+    # maxit reached -> NOT_CONVERGED with X the last iterate
+    m = oracle_mod.bminres(A, workloads.randn_rhs(A.n, 2, 3), tol=1e-12, maxit=5, xhist=5)
+    assert m.status == 1 and m.iters == 5 and np.array_equal(m.X, m.Xhist[4])
