@@ -29,9 +29,12 @@
  *       is created.  On a dependence a bench vector gets one more modified Gram-Schmidt pass
  *       against u_{j-p+1} .. u_{j+p-1} and the active removed vectors, is normalised and
  *       becomes u_{j+p}; h_{j+p,j} is set to 0 (so h_{j,j+p} = 0 by symmetry).
- *   R9  A removed vector (normalised w) is kept and new Lanczos vectors are orthogonalised
- *       against it for the next 2p iterations, after which it would have left the band
- *       (end of Sec. 5.1); its coefficients are not entered in H.
+ *   R9  A removed vector is kept and new Lanczos vectors are orthogonalised against it for the
+ *       next 2p iterations, after which it would have left the band (end of Sec. 5.1); its
+ *       coefficients are not entered in H.  The kept vector is w after one more MGS pass against
+ *       u_{j-p+1}..u_{j+p-1} and the removed vectors still active, normalised (dropped if
+ *       nothing is left).  It is kept only when ||w|| > 1e-12 ||A u_j||: for a dependence that is
+ *       exact to rounding, w is noise and carries no direction.
  *   R10 Lanczos orthogonalisation uses modified Gram-Schmidt in the order of Algorithm 1:
  *       known (symmetric) coefficients first, then the p new inner products.
  * The band QR uses Householder reflectors (Sec. 4) by default; qr_mode = 1 selects Givens
@@ -49,6 +52,10 @@
 #define OR_ERR_BREAKDOWN -4
 #define OR_ERR_BENCH_EXHAUSTED -5
 #define OR_ERR_NONFINITE -6
+
+/* reading R9: a removed vector is kept only for a near-dependence; at ||w|| <= 1e-12 ||A u_j|| the
+ * dependence is exact to rounding and w carries no direction */
+#define GHOST_FLOOR 1e-12
 
 typedef struct {
   int status;            /* OR_* code */
@@ -300,11 +307,21 @@ int oracle_bminres(int64_t n, const int32_t* rowptr, const int32_t* colidx, cons
       if (defl_iters && info->deflations < defl_cap) defl_iters[info->deflations] = j;
       info->deflations++;
       if (bench_next >= nb) { status = OR_ERR_BENCH_EXHAUSTED; --j; break; }
-      if (ghost && beta > 0.0) {
-        memcpy(Ghost + (size_t)n_ghost * n, w, sizeof(double) * n);
-        scal(n, 1.0 / beta, Ghost + (size_t)n_ghost * n);
-        ghost_born[n_ghost] = j;
-        n_ghost++;
+      if (ghost && beta > GHOST_FLOOR * normAu) {
+        /* reading R9: the kept vector is the part of w orthogonal to the window (one more MGS pass
+         * against u_{j-p+1}..u_{j+p-1} and the removed vectors active at j), normalised; for an
+         * exact dependence w is rounding noise with O(1) components along the window */
+        double* g = Ghost + (size_t)n_ghost * n;
+        memcpy(g, w, sizeof(double) * n);
+        for (int i = (j - p + 1 > 1 ? j - p + 1 : 1); i <= j + p - 1; ++i) mgs_step(n, USLOT(i), g);
+        for (int q = 0; q < n_ghost; ++q)
+          if (ghost_born[q] < j && j <= ghost_born[q] + 2 * p) mgs_step(n, Ghost + (size_t)q * n, g);
+        double ng = nrm2(n, g);
+        if (ng > 0.0) {
+          scal(n, 1.0 / ng, g);
+          ghost_born[n_ghost] = j;
+          n_ghost++;
+        }
       }
       memcpy(unew, Bench + (size_t)bench_next * n, sizeof(double) * n);
       bench_next++;

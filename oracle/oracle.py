@@ -83,7 +83,7 @@ class Result:
         return STATUS.get(self.status, str(self.status))
 
 
-def bminres(A, B, X0=None, tol=1e-10, maxit=1000, gamma=1e-8, bench=4, seed=0, ghost=True,
+def bminres(A, B, X0=None, tol=1e-10, maxit=1000, gamma=1e-8, bench=4, seed=0, ghost=False,
             qr="householder", hist=0, xhist=0, uhist=0) -> Result:
     """Run the oracle on CSR ``A`` (a ``workloads.CSR``) and row-major ``B`` (n, p)."""
     lib = _load()

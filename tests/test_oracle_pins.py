@@ -405,3 +405,25 @@ def test_zero_rhs_column_and_degenerate_sizes(oracle_mod, workloads):
     # maxit reached -> NOT_CONVERGED with X the last iterate
     m = oracle_mod.bminres(A, workloads.randn_rhs(A.n, 2, 3), tol=1e-12, maxit=5, xhist=5)
     assert m.status == 1 and m.iters == 5 and np.array_equal(m.X, m.Xhist[4])
+
+
+def test_removed_vector_retention_breaks_the_residual_recursion(oracle_mod, workloads):
+    """Reading of the end of Sec. 5.1: orthogonalising new Lanczos vectors against a removed vector
+    without entering the coefficients in H departs from the band Lanczos relation A U_j = U_{j+p} H_j
+    (the paper notes it no longer follows the derivation).  On a dependence at iteration 5 (p = 2)
+    the recursive residual then claims convergence while the true residual does not follow; without
+    retention both agree.  This is why retention is off by default."""
+    n = 300
+    rng = np.random.default_rng(11)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.linspace(0.6, 4.0, n) * np.where(np.arange(n) % 3 == 0, -1.0, 1.0)
+    A = workloads.dense_to_csr(0.5 * ((Q * lam) @ Q.T + ((Q * lam) @ Q.T).T))
+    noise = rng.standard_normal(n)
+    f1 = Q[:, :3] @ np.array([1.0, -0.7, 0.4]) + 1e-14 * noise
+    B = np.stack([f1, rng.standard_normal(n)], axis=1)
+    keep = oracle_mod.bminres(A, B, tol=1e-10, maxit=3000, ghost=True)
+    drop = oracle_mod.bminres(A, B, tol=1e-10, maxit=3000, ghost=False)
+    assert keep.defl_iters[:1] == [5] and drop.defl_iters[:1] == [5]
+    assert keep.status == 0 and drop.status == 0  # both stopping tests are met
+    assert oracle_mod.relres(A, B, drop.X).max() < 2e-10
+    assert oracle_mod.relres(A, B, keep.X).max() > 1e-6
