@@ -1,0 +1,1159 @@
+// Persistent cooperative kernel running one whole block MINRES solve (band Lanczos version,
+// Algorithm 2 of Soodhalter's paper) on the GPU.
+//
+// Execution model
+//   * One cooperative launch per solve.  Every block owns the same contiguous row range in every
+//     phase, so row-local updates need no grid synchronisation.
+//   * Per band iteration there is ONE streaming pass over the 2p-vector window: the update of
+//     iteration j (B step) fused with the known-coefficient subtraction and the inner products of
+//     iteration j+1 (A step).  Every p iterations the block product A [u_j .. u_{j+p-1}] runs,
+//     fused with the A step of the first iteration of the cycle, and the search directions and the
+//     iterate are updated once per cycle (p rank-1 updates of Eq. (approx-update) at once).
+//   * The single-pass inner products are classical Gram-Schmidt; they are turned into the
+//     modified Gram-Schmidt coefficients of Algorithm 1 exactly, through the Gram entries
+//     u_i . u_k of the window recorded when each vector is created (one triangular recurrence of
+//     p scalars).  Without it the window's rounding-level non-orthogonality is amplified every
+//     iteration.
+//   * After each pass every block reduces the per-block partial sums of ALL blocks in the same
+//     fixed order, so every block holds bit-identical coefficients and takes identical decisions
+//     (dependence test, band QR, convergence) without a broadcast.
+//   * Warp 0 of each block is a control warp: between passes it updates the coefficients with
+//     all 32 lanes, and DURING the next streaming pass it runs the band QR step of the iteration
+//     just finished (the QR only feeds the end-of-cycle direction update and the stopping test,
+//     which therefore lags one pass).  The other warps stream the vectors.
+//   * The band QR uses Givens rotations (Sec. 4 uses Householder reflectors; R differs only in row
+//     signs, X is the same).  The rotations of the last 2p columns are kept accumulated in an
+//     orthogonal 3p x 2p window (the accumulation suggested at the end of Sec. 4), so applying
+//     them to the new column is one small matrix-vector product; the p rotations of the new column
+//     come from prefix norms in closed form.
+//   * Lanczos vectors are stored unnormalised with a per-slot scale sigma_i (u_i = sigma_i raw_i).
+//
+// Data layout (all vectors have stride `ld` elements, V = double or float):
+//   U     2p ring slots, u_i in slot i mod 2p        (band Lanczos FIFO, Sec. 7)
+//   W     p slots: block product, overwritten in place by the partly orthogonalised w'
+//   M     2p ring slots, m_i in slot i mod 2p        (search-direction FIFO, Sec. 7)
+//   Bench NB bench vectors; Ghost NB removed vectors (normalised)
+//   X     row-major n x p iterate (FP64 mode) or correction D (mixed mode, zeroed on entry)
+// U, M and Ghost must be zero on entry.
+#pragma once
+#include "common.cuh"
+
+namespace bmr {
+
+template <typename V>
+struct SolveArgs {
+  int64_t n;
+  int64_t ld;
+  int p;
+  int nbench;
+  int ghost;
+  int maxit;
+  double tol;
+  double gamma;
+  uint64_t seed;
+  const int32_t* rowptr;
+  const int32_t* colidx;
+  const V* vals;
+  const V* F;  // p vectors: initial block residual F0
+  V* X;
+  V* U;
+  V* W;
+  V* M;
+  V* Bench;
+  V* Ghost;
+  double* part;  // [2][NVMAX][nblocks]
+  Ctl* ctl;
+  double* rho_hist;  // optional: [hist_cap][p] recursive residual norms
+  int hist_cap;
+  unsigned long long barrier_limit_ns;
+};
+
+template <int PM>
+struct Layout {
+  static constexpr int GR = (PM > 1) ? PM - 1 : 1;  // Gram entries kept per Lanczos vector
+  // fused pass (B step of j + A step of j+1)
+  static constexpr int BA_NRM = 0, BA_W1 = 1, BA_DOT = 2, BA_GR = 2 + PM, BA_BEN = 2 + PM + GR,
+                       BA_GH = 2 + PM + GR + NBMAX;
+  static constexpr int BA_N = 2 + PM + GR + 2 * NBMAX;
+  // block-product pass
+  static constexpr int SP_NRM = 0, SP_DOT = 1, SP_GH = 1 + PM, SP_N = 1 + PM + NBMAX;
+  // substitution pass D2
+  static constexpr int D2_NRM = 0, D2_BEN = 1, D2_GR = 1 + NBMAX, D2_N = 1 + NBMAX + GR;
+  static constexpr int NVMAX = (2 * PM + NBMAX > BA_N) ? 2 * PM + NBMAX : BA_N;
+};
+
+template <int PM>
+struct __align__(16) Shared {
+  int cycle, status, qstop, qstatus;
+  int bench_next, n_ghost, deflations, setup_defl;
+  int ghost_born[NBMAX];
+  double beta;                  // h_{j+p,j} of the last pass (0 after a substitution)
+  double sigq;                  // sigma_j of the column handed to the QR warp
+  double f0n[PM];
+  double thr2[PM];              // (tol * ||f0_i||)^2
+  double inv2[PM];              // 1 / ||f0_i||^2 (0 for a zero column)
+  double rho2[PM];              // squared recursive residuals of the last QR step
+  double sigma[2 * PM];         // scale of U slots (slot = i mod 2p)
+  double hsub[PM][PM];          // C queue: hsub[i mod p][k-1] = h_{i+k,i}
+  double hdiag[2];              // h_{i,i} for i = j, j+1 (slot i & 1)
+  double normAu2[2];            // ||A u_i||^2, same slots
+  double coefB[PM];             // B step of j: h_{j+k,j} sigma_{j+k}
+  double coefA[PM];             // A step of j+1: h_{j+1,i} sigma_i, i = j+1-p+k
+  double cgB[NBMAX];            // removed-vector coefficients of the B step
+  double gram[2 * PM][Layout<PM>::GR];  // gram[i mod 2p][m-1] = u_i . u_{i-m}, m = 1..p-1
+  double P[3 * PM][2 * PM];     // accumulated rotations, ring indexed [row mod 3p][col mod 2p]
+  double Sh[PM + 1][PM];        // rows j..j+p of Shat, ring indexed by row mod (p+1)
+  double colq[2 * PM + 1];      // column j of H-bar (rows j-p..j+p) handed to the QR warp
+  double y[3 * PM + 1];         // rotated column, rows j-2p..j+p
+  double pref[PM + 1], rinv[PM + 1], gc[PM + 1], gs[PM + 1];
+  double rjj[PM];               // r_{j,j} of the iterations of the current cycle
+  double Zc[PM][PM];            // z_j of the current cycle
+  double bc[NBMAX][2][PM];      // bench maintenance coefficients, by cycle parity
+  double dirA[PM];              // direction recurrence coefficients of the cycle:
+  union {                       // dirB[l][q] multiplies m_{j0+l-2PM+q}; S only during set-up
+    double dirB[PM][2 * PM];
+    double S[PM][PM];           // initial QR factor
+  };
+  double qd[PM], qe[PM];        // set-up Gram-Schmidt coefficients
+  double red[Layout<PM>::NVMAX];   // values of the last grid reduction
+  double rba[Layout<PM>::NVMAX];   // saved values of the last fused pass
+  double s2[Layout<PM>::NVMAX][32];
+  double d4[Layout<PM>::NVMAX][4];
+};
+
+template <typename V, int PM, int NT>
+struct Engine {
+  using A = V;  // per-thread accumulation in the vector precision
+  using LY = Layout<PM>;
+  static constexpr int NVMAX = LY::NVMAX;
+  static constexpr int NS = NT - 32;  // streaming threads (warps 1..NT/32-1)
+  static constexpr int RCH = 16;      // values per chunk of a block reduction
+  const SolveArgs<V>& a;
+  Shared<PM>& sh;
+  A* scr;  // [RCH][NS] scratch for block reductions
+  int64_t rb, re;
+  int nblocks;
+  int buf;
+  int p;
+  int lane, warp;
+  unsigned long long t_mark;
+
+  __device__ Engine(const SolveArgs<V>& args, Shared<PM>& s, A* scratch)
+      : a(args), sh(s), scr(scratch), buf(0), p(args.p), t_mark(0) {
+    nblocks = gridDim.x;
+    int64_t chunk = (a.n + nblocks - 1) / nblocks;
+    chunk = (chunk + 31) / 32 * 32;
+    rb = (int64_t)blockIdx.x * chunk;
+    re = rb + chunk;
+    if (re > a.n) re = a.n;
+    if (rb > a.n) rb = a.n;
+    lane = threadIdx.x & 31;
+    warp = threadIdx.x >> 5;
+  }
+
+  // first row of this streaming thread (rows advance by NS); control-warp threads get re
+  __device__ __forceinline__ int64_t row0() const { return warp == 0 ? re : rb + (threadIdx.x - 32); }
+
+  __device__ __forceinline__ int ring2p(int i) const { return ((i % (2 * p)) + 2 * p) % (2 * p); }
+  __device__ __forceinline__ V* uslot(int i) const { return a.U + (int64_t)ring2p(i) * a.ld; }
+  __device__ __forceinline__ V* mslot(int i) const { return a.M + (int64_t)ring2p(i) * a.ld; }
+  __device__ __forceinline__ double& sig(int i) { return sh.sigma[ring2p(i)]; }
+  __device__ __forceinline__ V* wslot(int k) const { return a.W + (int64_t)k * a.ld; }
+  __device__ __forceinline__ V* bench(int k) const { return a.Bench + (int64_t)k * a.ld; }
+  __device__ __forceinline__ V* ghostv(int g) const { return a.Ghost + (int64_t)g * a.ld; }
+  __device__ __forceinline__ bool ghost_active(int g, int jj) const {
+    return g < sh.n_ghost && sh.ghost_born[g] < jj && jj <= sh.ghost_born[g] + 2 * p;
+  }
+
+  // block 0's timeline, measured by its first streaming thread
+  __device__ __forceinline__ void tick(unsigned long long& bucket) {
+    if (blockIdx.x == 0 && threadIdx.x == 32) {
+      unsigned long long t = gtimer();
+      bucket += t - t_mark;
+      t_mark = t;
+    }
+  }
+  __device__ __forceinline__ void set_status(int st) {
+    if (threadIdx.x == 0 && sh.status == ST_OK) sh.status = st;
+    __syncthreads();
+  }
+
+  // ---- reduction of nv per-thread values over the whole grid -> sh.red[0..nv) ----------------
+  // Inside the block: transpose the streaming threads' values through shared memory and sum in a
+  // fixed order; across blocks: every block sums the per-block partials of all blocks in the same
+  // fixed order.  Returns false if a grid barrier failed.
+  template <int NVC>
+  __device__ bool reduce(const A (&acc)[NVC], int nv) {
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int c0 = 0; c0 < NVC; c0 += RCH) {
+      if (c0 < nv) {
+        if (warp > 0) {
+#pragma unroll
+          for (int v = 0; v < RCH; ++v)
+            if (c0 + v < NVC && c0 + v < nv) scr[v * NS + tid - 32] = acc[c0 + v];
+        }
+        __syncthreads();
+        const int cn = (nv - c0 < RCH) ? nv - c0 : RCH;
+        for (int task = tid; task < cn * 32; task += NT) {
+          int v = task >> 5, l = task & 31;
+          A s = scr[v * NS + l];
+#pragma unroll
+          for (int q = 1; q < NS / 32; ++q) s += scr[v * NS + l + 32 * q];
+          sh.s2[c0 + v][l] = (double)s;
+        }
+        __syncthreads();
+      }
+    }
+    fold32(nv);
+    if (nblocks == 1) {
+      for (int v = tid; v < nv; v += NT) sh.red[v] = (sh.d4[v][0] + sh.d4[v][1]) + (sh.d4[v][2] + sh.d4[v][3]);
+      __syncthreads();
+      return true;
+    }
+    double* part = a.part + (int64_t)buf * NVMAX * nblocks;
+    for (int v = tid; v < nv; v += NT)
+      part[(int64_t)v * nblocks + blockIdx.x] = (sh.d4[v][0] + sh.d4[v][1]) + (sh.d4[v][2] + sh.d4[v][3]);
+    buf ^= 1;
+    if (!grid_barrier(a.ctl, nblocks, a.barrier_limit_ns)) return false;
+    for (int task = tid; task < nv * 32; task += NT) {
+      int v = task >> 5, l = task & 31;
+      const double* pv = part + (int64_t)v * nblocks;
+      double s = 0.0;
+      for (int b = l; b < nblocks; b += 32) s += pv[b];
+      sh.s2[v][l] = s;
+    }
+    __syncthreads();
+    fold32(nv);
+    for (int v = tid; v < nv; v += NT) sh.red[v] = (sh.d4[v][0] + sh.d4[v][1]) + (sh.d4[v][2] + sh.d4[v][3]);
+    __syncthreads();
+    return true;
+  }
+  __device__ __forceinline__ void fold32(int nv) {
+    for (int task = threadIdx.x; task < nv * 4; task += NT) {
+      int v = task >> 2, q = task & 3;
+      const double* s = sh.s2[v] + 8 * q;
+      sh.d4[v][q] = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+    }
+    __syncthreads();
+  }
+
+  // ---- set-up ---------------------------------------------------------------------------------
+  __device__ bool setup_norms() {
+    A acc[PM];
+#pragma unroll
+    for (int k = 0; k < PM; ++k) acc[k] = 0;
+    for (int64_t r = row0(); r < re; r += NS) {
+#pragma unroll
+      for (int k = 0; k < PM; ++k)
+        if (k < p) {
+          A f = a.F[(int64_t)k * a.ld + r];
+          acc[k] += f * f;
+        }
+    }
+    if (!reduce(acc, p)) return false;
+    if (threadIdx.x < p) {
+      const int i = threadIdx.x;
+      const double f2 = sh.red[i];
+      sh.f0n[i] = sqrt(f2);
+      sh.thr2[i] = a.tol * a.tol * f2;
+      sh.inv2[i] = (f2 > 0.0) ? 1.0 / f2 : 0.0;
+    }
+    // bench vectors, drawn before the iteration (Sec. 5.1)
+    for (int k = 0; k < a.nbench; ++k)
+      for (int64_t r = row0(); r < re; r += NS) bench(k)[r] = (V)bench_value(a.seed, k, a.n, r);
+    __syncthreads();
+    return true;
+  }
+
+  // One column of the initial economy QR F0 = U_p S (Eq. (init-QR)): classical Gram-Schmidt with
+  // one re-orthogonalisation, from `src` into the slot of u_{i+1}.  Leaves the squared norm in
+  // sh.red[0] and the raw inner products with the remaining bench vectors in sh.red[1 + b].
+  __device__ bool setup_column(int i, const V* src, bool record_S) {
+    const int tid = threadIdx.x;
+    if (tid < PM) {
+      sh.qd[tid] = 0.0;
+      sh.qe[tid] = 0.0;
+    }
+    __syncthreads();
+    if (i > 0) {
+      {
+        A acc[PM];
+#pragma unroll
+        for (int k = 0; k < PM; ++k) acc[k] = 0;
+        for (int64_t r = row0(); r < re; r += NS) {
+          A s = src[r];
+#pragma unroll
+          for (int k = 0; k < PM; ++k)
+            if (k < i) acc[k] += (A)uslot(k + 1)[r] * s;
+        }
+        if (!reduce(acc, i)) return false;
+        if (tid < i) sh.qd[tid] = sig(tid + 1) * sig(tid + 1) * sh.red[tid];
+        __syncthreads();
+      }
+      {
+        A cf[PM];
+#pragma unroll
+        for (int k = 0; k < PM; ++k) cf[k] = (k < i) ? (A)sh.qd[k] : (A)0;
+        A acc[PM];
+#pragma unroll
+        for (int k = 0; k < PM; ++k) acc[k] = 0;
+        for (int64_t r = row0(); r < re; r += NS) {
+          A v = src[r];
+          A uk[PM];
+#pragma unroll
+          for (int k = 0; k < PM; ++k) {
+            uk[k] = (k < i) ? (A)uslot(k + 1)[r] : (A)0;
+            v -= cf[k] * uk[k];
+          }
+#pragma unroll
+          for (int k = 0; k < PM; ++k)
+            if (k < i) acc[k] += uk[k] * v;
+        }
+        if (!reduce(acc, i)) return false;
+        if (tid < i) sh.qe[tid] = sig(tid + 1) * sig(tid + 1) * sh.red[tid];
+        __syncthreads();
+      }
+    }
+    A cf[PM];
+#pragma unroll
+    for (int k = 0; k < PM; ++k) cf[k] = (k < i) ? (A)(sh.qd[k] + sh.qe[k]) : (A)0;
+    constexpr int NVC = 1 + NBMAX;
+    A acc[NVC];
+#pragma unroll
+    for (int k = 0; k < NVC; ++k) acc[k] = 0;
+    const int b0 = sh.bench_next, nb = a.nbench;
+    V* dst = uslot(i + 1);
+    for (int64_t r = row0(); r < re; r += NS) {
+      A v = src[r];
+#pragma unroll
+      for (int k = 0; k < PM; ++k)
+        if (k < i) v -= cf[k] * (A)uslot(k + 1)[r];
+      dst[r] = (V)v;
+      acc[0] += v * v;
+#pragma unroll
+      for (int b = 0; b < NBMAX; ++b)
+        if (b >= b0 && b < nb) acc[1 + b] += (A)bench(b)[r] * v;
+    }
+    if (!reduce(acc, 1 + nb)) return false;
+    if (record_S && tid < i) sh.S[tid][i] = (sh.qd[tid] + sh.qe[tid]) / sig(tid + 1);
+    __syncthreads();
+    return true;
+  }
+
+  // ---- block product fused with the A step of iteration j0 (first pass of a cycle) ------------
+  // W_k = A u_{j0+k}; w'_{j0} = W_0 - sum_{i<j0} h_{j0,i} u_i (into W slot 0); inner products
+  // u_{j0+k} . w'_{j0}; removed-vector products; ||W_0||^2.  The control warp runs the QR step of
+  // iteration qr_j (if > 0) meanwhile.
+  __device__ bool pass_spmm(int j0, int qr_j, int qr_l) {
+    A acc[LY::SP_N];
+#pragma unroll
+    for (int k = 0; k < LY::SP_N; ++k) acc[k] = 0;
+    int ng = 0;
+#pragma unroll
+    for (int g = 0; g < NBMAX; ++g)
+      if (g < sh.n_ghost) ng = g + 1;
+    if (warp == 0) {
+      if (qr_j > 0) qr_warp(qr_j, qr_l);
+    } else {
+      A cA[PM], sg[PM];
+      const V* usrc[PM];
+      const V* uknown[PM];
+#pragma unroll
+      for (int k = 0; k < PM; ++k) {
+        cA[k] = (k < p) ? (A)sh.coefA[k] : (A)0;
+        sg[k] = (k < p) ? (A)sig(j0 + k) : (A)0;
+        usrc[k] = uslot(j0 + k);
+        uknown[k] = uslot(j0 - p + k);
+      }
+      const bool has_known = (j0 > 1);
+      bool gact[NBMAX];
+#pragma unroll
+      for (int g = 0; g < NBMAX; ++g) gact[g] = ghost_active(g, j0);
+      for (int64_t r = row0(); r < re; r += NS) {
+        A wk[PM];
+#pragma unroll
+        for (int k = 0; k < PM; ++k) wk[k] = 0;
+        const int32_t k0 = __ldg(a.rowptr + r), k1 = __ldg(a.rowptr + r + 1);
+        for (int32_t q = k0; q < k1; ++q) {
+          const int32_t c = __ldg(a.colidx + q);
+          const A v = __ldg(a.vals + q);
+#pragma unroll
+          for (int k = 0; k < PM; ++k)
+            if (k < p) wk[k] += v * (A)usrc[k][c];
+        }
+#pragma unroll
+        for (int k = 0; k < PM; ++k) wk[k] *= sg[k];
+        A wp = wk[0];
+        if (has_known) {
+#pragma unroll
+          for (int k = 0; k < PM; ++k)
+            if (k < p) wp -= cA[k] * (A)uknown[k][r];
+        }
+        wslot(0)[r] = (V)wp;
+#pragma unroll
+        for (int k = 1; k < PM; ++k)
+          if (k < p) wslot(k)[r] = (V)wk[k];
+#pragma unroll
+        for (int k = 0; k < PM; ++k)
+          if (k < p) acc[LY::SP_DOT + k] += (A)usrc[k][r] * wp;
+#pragma unroll
+        for (int g = 0; g < NBMAX; ++g)
+          if (gact[g]) acc[LY::SP_GH + g] += (A)ghostv(g)[r] * wp;
+        acc[LY::SP_NRM] += wk[0] * wk[0];
+      }
+    }
+    tick(a.ctl->t_stream);
+    if (!reduce(acc, ng > 0 ? LY::SP_GH + ng : LY::SP_GH)) return false;
+    tick(a.ctl->t_reduce);
+    return true;
+  }
+
+  // ---- fused pass of iteration j: B step of j (+ A step of j+1 when hasA) ---------------------
+  // B:  w_j = w'_j - sum_{k<p} h_{j+k,j} u_{j+k} - sum_g c_g g   -> raw slot of u_{j+p}
+  // A:  w'_{j+1} = W_{t+1} - sum_{i=j+1-p}^{j} h_{j+1,i} u_i (in place), and its inner products
+  //     with u_{j+1} .. u_{j+p-1}, with w_j (the future u_{j+p}, unnormalised), with the removed
+  //     vectors active at j+1.  Also ||w_j||^2, ||W_{t+1}||^2, w_j . u_{j+k} (Gram entries) and
+  //     bench . w_j.  The control warp runs the QR step of iteration qr_j (if > 0) meanwhile.
+  __device__ bool pass_ba(int j, int t, bool hasA, int qr_j, int qr_l) {
+    A acc[LY::BA_N];
+#pragma unroll
+    for (int k = 0; k < LY::BA_N; ++k) acc[k] = 0;
+    int ng = 0;
+#pragma unroll
+    for (int g = 0; g < NBMAX; ++g)
+      if (g < sh.n_ghost) ng = g + 1;
+    const int nb = a.nbench;
+    if (warp == 0) {
+      if (qr_j > 0) qr_warp(qr_j, qr_l);
+    } else {
+      A cB[PM], cA[PM], cgb[NBMAX];
+      const V* ub[PM];
+      const V* ua[PM];
+#pragma unroll
+      for (int k = 0; k < PM; ++k) {
+        cB[k] = (k < p) ? (A)sh.coefB[k] : (A)0;
+        cA[k] = (k < p - 1) ? (A)sh.coefA[k] : (A)0;
+        ub[k] = uslot(j + k);
+        ua[k] = uslot(j + 1 - p + k);
+      }
+      const A cA_last = (A)sh.coefA[p - 1];  // multiplies u_j, loaded as ub[0]
+      bool gB[NBMAX], gA[NBMAX];
+#pragma unroll
+      for (int g = 0; g < NBMAX; ++g) {
+        gB[g] = ghost_active(g, j);
+        gA[g] = ghost_active(g, j + 1);
+        cgb[g] = gB[g] ? (A)sh.cgB[g] : (A)0;
+      }
+      const bool known_ok = (j + 1 - p >= 1);  // every u_i with i = j+1-p+k, k < p-1, exists
+      const int b0 = sh.bench_next;
+      V* wout = uslot(j + p);
+      const V* wcur = wslot(t);
+      V* wnext = wslot(t + 1 < p ? t + 1 : t);
+      for (int64_t r = row0(); r < re; r += NS) {
+        A w = wcur[r];
+        A ubv[PM];
+#pragma unroll
+        for (int k = 0; k < PM; ++k)
+          if (k < p) {
+            ubv[k] = ub[k][r];
+            w -= cB[k] * ubv[k];
+          }
+#pragma unroll
+        for (int g = 0; g < NBMAX; ++g)
+          if (gB[g]) w -= cgb[g] * (A)ghostv(g)[r];
+        wout[r] = (V)w;
+        acc[LY::BA_NRM] += w * w;
+#pragma unroll
+        for (int k = 1; k < PM; ++k)
+          if (k < p) acc[LY::BA_GR + k - 1] += w * ubv[k];
+#pragma unroll
+        for (int b = 0; b < NBMAX; ++b)
+          if (b >= b0 && b < nb) acc[LY::BA_BEN + b] += (A)bench(b)[r] * w;
+        if (hasA) {
+          A w1 = wnext[r];
+          acc[LY::BA_W1] += w1 * w1;
+          if (known_ok) {
+#pragma unroll
+            for (int k = 0; k < PM - 1; ++k)
+              if (k < p - 1) w1 -= cA[k] * (A)ua[k][r];
+          } else {
+#pragma unroll
+            for (int k = 0; k < PM - 1; ++k)
+              if (k < p - 1 && j + 1 - p + k >= 1) w1 -= cA[k] * (A)ua[k][r];
+          }
+          w1 -= cA_last * ubv[0];
+          wnext[r] = (V)w1;
+#pragma unroll
+          for (int k = 0; k < PM - 1; ++k)
+            if (k < p - 1) acc[LY::BA_DOT + k] += ubv[k + 1] * w1;
+          acc[LY::BA_DOT + PM - 1] += w * w1;
+#pragma unroll
+          for (int g = 0; g < NBMAX; ++g)
+            if (gA[g]) acc[LY::BA_GH + g] += (A)ghostv(g)[r] * w1;
+        }
+      }
+    }
+    tick(a.ctl->t_stream);
+    const int nv = ng > 0 ? LY::BA_GH + ng : LY::BA_BEN + nb;
+    if (!reduce(acc, nv)) return false;
+    for (int v = threadIdx.x; v < NVMAX; v += NT) sh.rba[v] = (v < nv) ? sh.red[v] : 0.0;
+    __syncthreads();
+    tick(a.ctl->t_reduce);
+    return true;
+  }
+
+  // ---- substitution of a dependent vector (Sec. 5.1) at iteration j ---------------------------
+  // When new_ghost >= 0 the removed w_j is kept: its part orthogonal to u_{j-p+1} .. u_{j+p-1} and
+  // to the removed vectors active at j, normalised (dropped if nothing is left).  Bench vector bk
+  // is orthogonalised (one classical Gram-Schmidt pass) against u_{j-p+1} .. u_{j+p-1} and the
+  // removed vectors active at j+1, normalised and stored as u_{j+p}.  Patches the saved A-step
+  // values.
+  __device__ bool substitute(int j, int t, bool hasA, int bk, int new_ghost) {
+    const int tid = threadIdx.x;
+    const int cyc = sh.cycle;
+    const V* bsrc = bench(bk);
+    V* dst = uslot(j + p);
+    A sg_new = 0;
+    if (new_ghost >= 0) {
+      bool gB[NBMAX];
+      int ngB = 0;
+#pragma unroll
+      for (int g = 0; g < NBMAX; ++g) {
+        gB[g] = ghost_active(g, j);
+        if (gB[g]) ngB = g + 1;
+      }
+      // G1: inner products of w_j with the window and the removed vectors active at j
+      {
+        constexpr int NVC = 2 * PM + NBMAX;
+        A acc[NVC];
+#pragma unroll
+        for (int k = 0; k < NVC; ++k) acc[k] = 0;
+        for (int64_t r = row0(); r < re; r += NS) {
+          A wv = dst[r];
+#pragma unroll
+          for (int k = 0; k < 2 * PM - 1; ++k)
+            if (k < 2 * p - 1 && j - p + 1 + k >= 1) acc[k] += (A)uslot(j - p + 1 + k)[r] * wv;
+#pragma unroll
+          for (int g = 0; g < NBMAX; ++g)
+            if (gB[g]) acc[2 * PM + g] += (A)ghostv(g)[r] * wv;
+        }
+        if (!reduce(acc, 2 * PM + ngB)) return false;
+      }
+      A cw[2 * PM], cg[NBMAX];
+#pragma unroll
+      for (int k = 0; k < 2 * PM; ++k) {
+        int i = j - p + 1 + k;
+        cw[k] = (k < 2 * p - 1 && i >= 1) ? (A)(sig(i) * sig(i) * sh.red[k]) : (A)0;
+      }
+#pragma unroll
+      for (int g = 0; g < NBMAX; ++g) cg[g] = gB[g] ? (A)sh.red[2 * PM + g] : (A)0;
+      __syncthreads();
+      // G2: the kept vector (unnormalised) and its squared norm
+      {
+        A acc[1] = {0};
+        for (int64_t r = row0(); r < re; r += NS) {
+          A v = dst[r];
+#pragma unroll
+          for (int k = 0; k < 2 * PM - 1; ++k)
+            if (k < 2 * p - 1 && j - p + 1 + k >= 1) v -= cw[k] * (A)uslot(j - p + 1 + k)[r];
+#pragma unroll
+          for (int g = 0; g < NBMAX; ++g)
+            if (gB[g]) v -= cg[g] * (A)ghostv(g)[r];
+          ghostv(new_ghost)[r] = (V)v;
+          acc[0] += v * v;
+        }
+        if (!reduce(acc, 1)) return false;
+      }
+      const double g2 = sh.red[0];
+      if (g2 > 0.0 && isfinite(g2)) {
+        sg_new = (A)rsqrt(g2);
+      } else {  // nothing left to keep
+        __syncthreads();
+        if (tid == 0) sh.n_ghost = new_ghost;
+        __syncthreads();
+        new_ghost = -1;
+      }
+    }
+    bool gA[NBMAX];
+    int ng = 0;
+#pragma unroll
+    for (int g = 0; g < NBMAX; ++g) {
+      gA[g] = ghost_active(g, j + 1);
+      if (g < sh.n_ghost) ng = g + 1;
+    }
+    // D1: normalise the kept vector; inner products of the bench vector with window and ghosts
+    {
+      constexpr int NVC = 2 * PM + NBMAX;
+      A acc[NVC];
+#pragma unroll
+      for (int k = 0; k < NVC; ++k) acc[k] = 0;
+      for (int64_t r = row0(); r < re; r += NS) {
+        A bv = bsrc[r];
+        if (new_ghost >= 0) ghostv(new_ghost)[r] = (V)((A)ghostv(new_ghost)[r] * sg_new);
+#pragma unroll
+        for (int k = 0; k < 2 * PM - 1; ++k)
+          if (k < 2 * p - 1 && j - p + 1 + k >= 1) acc[k] += (A)uslot(j - p + 1 + k)[r] * bv;
+#pragma unroll
+        for (int g = 0; g < NBMAX; ++g)
+          if (gA[g]) acc[2 * PM + g] += (A)ghostv(g)[r] * bv;
+      }
+      if (!reduce(acc, 2 * PM + ng)) return false;
+    }
+    A cw[2 * PM], cg[NBMAX];
+#pragma unroll
+    for (int k = 0; k < 2 * PM; ++k) {
+      int i = j - p + 1 + k;
+      cw[k] = (k < 2 * p - 1 && i >= 1) ? (A)(sig(i) * sig(i) * sh.red[k]) : (A)0;
+    }
+#pragma unroll
+    for (int g = 0; g < NBMAX; ++g) cg[g] = gA[g] ? (A)sh.red[2 * PM + g] : (A)0;
+    __syncthreads();
+    // D2: the substitute, its norm, its inner products with the remaining bench vectors and with
+    //     u_{j+1} .. u_{j+p-1} (Gram entries)
+    {
+      constexpr int NVC = LY::D2_N;
+      A acc[NVC];
+#pragma unroll
+      for (int k = 0; k < NVC; ++k) acc[k] = 0;
+      const int nb = a.nbench;
+      for (int64_t r = row0(); r < re; r += NS) {
+        A v = bsrc[r];
+#pragma unroll
+        for (int k = 0; k < 2 * PM - 1; ++k)
+          if (k < 2 * p - 1 && j - p + 1 + k >= 1) v -= cw[k] * (A)uslot(j - p + 1 + k)[r];
+#pragma unroll
+        for (int g = 0; g < NBMAX; ++g)
+          if (gA[g]) v -= cg[g] * (A)ghostv(g)[r];
+        dst[r] = (V)v;
+        acc[LY::D2_NRM] += v * v;
+#pragma unroll
+        for (int b = 0; b < NBMAX; ++b)
+          if (b > bk && b < nb) acc[LY::D2_BEN + b] += (A)bench(b)[r] * v;
+#pragma unroll
+        for (int k = 1; k < PM; ++k)
+          if (k < p) acc[LY::D2_GR + k - 1] += v * (A)uslot(j + k)[r];
+      }
+      if (!reduce(acc, LY::D2_N)) return false;
+    }
+    if (tid == 0) {
+      double nr2 = sh.red[LY::D2_NRM];
+      if (!(nr2 > 0.0) || !isfinite(nr2)) {
+        sh.status = ST_ERR_BENCH;
+      } else {
+        double s = rsqrt(nr2);
+        sig(j + p) = s;
+        for (int b = bk + 1; b < a.nbench; ++b) sh.bc[b][(cyc + 1) & 1][t] = s * s * sh.red[LY::D2_BEN + b];
+        for (int k = 1; k < p; ++k) sh.gram[ring2p(j + p)][p - k - 1] = s * sig(j + k) * sh.red[LY::D2_GR + k - 1];
+      }
+    }
+    __syncthreads();
+    if (sh.status != ST_OK) return true;
+    // D3: inner products of w'_{j+1} with the new u_{j+p} and with the new removed vector
+    if (hasA) {
+      A acc[2] = {0, 0};
+      const V* w1 = wslot(t + 1);
+      for (int64_t r = row0(); r < re; r += NS) {
+        A x = w1[r];
+        acc[0] += (A)dst[r] * x;
+        if (new_ghost >= 0) acc[1] += (A)ghostv(new_ghost)[r] * x;
+      }
+      if (!reduce(acc, 2)) return false;
+      if (tid == 0) {
+        sh.rba[LY::BA_DOT + PM - 1] = sh.red[0];
+        if (new_ghost >= 0) sh.rba[LY::BA_GH + new_ghost] = sh.red[1];
+      }
+      __syncthreads();
+    }
+    return true;
+  }
+
+  // ---- blocked direction and iterate update for the L iterations of a cycle -----------------
+  // m_j = (u_j - sum_{i=j-2p}^{j-1} r_{i,j} m_i) / r_{j,j}   (Eq. (search-dir-comp))
+  // X  += sum_l m_{j0+l} z_{j0+l}^T                           (Eq. (approx-update), blocked)
+  // bench vectors lose their components along u_{j0} .. u_{j0+p-1} (coefficients of parity cyc).
+  __device__ void pass_dir(int j0, int L, int cyc, bool update_bench) {
+    if (warp > 0) {
+      const int nb = a.nbench, b0 = sh.bench_next;
+      const V* mold[2 * PM];
+      bool mvalid[2 * PM];
+#pragma unroll
+      for (int q = 0; q < 2 * PM; ++q) {
+        int i = j0 - 2 * PM + q;  // m_i held at window position q
+        mvalid[q] = (q >= 2 * PM - 2 * p) && i >= 1;
+        mold[q] = mslot(i);
+      }
+      for (int64_t r = row0(); r < re; r += NS) {
+        A mw[3 * PM];
+#pragma unroll
+        for (int q = 0; q < 2 * PM; ++q) mw[q] = mvalid[q] ? (A)mold[q][r] : (A)0;
+        A uv[PM];
+#pragma unroll
+        for (int l = 0; l < PM; ++l) uv[l] = (l < p) ? (A)uslot(j0 + l)[r] : (A)0;
+#pragma unroll
+        for (int l = 0; l < PM; ++l) {
+          if (l < L) {
+            A m = (A)sh.dirA[l] * uv[l];
+#pragma unroll
+            for (int q = 0; q < 2 * PM; ++q) m += (A)sh.dirB[l][q] * mw[l + q];
+            mw[2 * PM + l] = m;
+            mslot(j0 + l)[r] = (V)m;
+          } else {
+            mw[2 * PM + l] = 0;
+          }
+        }
+        V* xr = a.X + r * (int64_t)p;
+#pragma unroll
+        for (int c = 0; c < PM; ++c)
+          if (c < p) {
+            A s = xr[c];
+#pragma unroll
+            for (int l = 0; l < PM; ++l)
+              if (l < L) s += mw[2 * PM + l] * (A)sh.Zc[l][c];
+            xr[c] = (V)s;
+          }
+        if (update_bench) {
+#pragma unroll
+          for (int b = 0; b < NBMAX; ++b)
+            if (b >= b0 && b < nb) {
+              A v = bench(b)[r];
+#pragma unroll
+              for (int l = 0; l < PM; ++l)
+                if (l < p) v -= (A)sh.bc[b][cyc & 1][l] * uv[l];
+              bench(b)[r] = (V)v;
+            }
+        }
+      }
+    }
+    __syncthreads();
+    tick(a.ctl->t_stream);
+  }
+
+  // ---- control warp: coefficients between passes --------------------------------------------
+  // Modified Gram-Schmidt coefficients (Algorithm 1 order k = 0..p-1) from classical inner
+  // products d_k = u_{first+k} . w:  h_k = d_k - sum_{i<k} h_i (u_{first+k} . u_{first+i}).
+  // Lane k holds d_k on entry and h_k on exit (lanes >= p hold 0).
+  __device__ double mgs_lanes(double d, int first) {
+    const double* g = sh.gram[ring2p(first + (lane < p ? lane : 0))];
+    for (int i = 0; i < p - 1; ++i) {
+      double hi = __shfl_sync(0xffffffffu, d, i);
+      if (lane > i && lane < p) d -= hi * g[lane - i - 1];
+    }
+    return d;
+  }
+
+  // known coefficients of the A step of iteration jn: coefA[k] = h_{jn,i} sigma_i, i = jn-p+k
+  __device__ void ctl_coefA(int jn) {
+    if (lane < p) {
+      const int i = jn - p + lane;
+      sh.coefA[lane] = (i >= 1) ? sh.hsub[i % p][jn - i - 1] * sig(i) : 0.0;
+    }
+  }
+
+  // results of an A step for iteration jn from raw inner products dr (lane k: raw_{jn+k} . w')
+  __device__ void ctl_astep(int jn, double dr) {
+    double d = (lane < p) ? sig(jn + (lane < p ? lane : 0)) * dr : 0.0;
+    const double h = mgs_lanes(d, jn);
+    if (lane < p) {
+      if (lane == 0)
+        sh.hdiag[jn & 1] = h;
+      else
+        sh.hsub[jn % p][lane - 1] = h;
+      sh.coefB[lane] = h * sig(jn + lane);
+    }
+  }
+
+  // after the fused pass of iteration jj (all of warp 0; sh.beta = h_{jj+p,jj} already final)
+  __device__ void ctl_after_ba(int jj, int t, bool hasA) {
+    const double beta = sh.beta;
+    // column jj of H-bar, rows jj-p .. jj+p, for the QR warp (known entries from the C queue)
+    for (int k = lane; k <= 2 * p; k += 32) {
+      double v;
+      if (k < p) {
+        const int i = jj - p + k;
+        v = (i >= 1) ? sh.hsub[i % p][jj - i - 1] : 0.0;
+      } else if (k == p) {
+        v = sh.hdiag[jj & 1];
+      } else if (k < 2 * p) {
+        v = sh.hsub[jj % p][k - p - 1];
+      } else {
+        v = beta;
+      }
+      sh.colq[k] = v;
+    }
+    if (lane == 0) sh.sigq = sig(jj);
+    __syncwarp();
+    if (lane == 0) sh.hsub[jj % p][p - 1] = beta;  // h_{jj,jj-p} was read above
+    if (hasA) {
+      const double dr =
+          (lane < p - 1) ? sh.rba[LY::BA_DOT + lane] : ((lane == p - 1) ? sh.rba[LY::BA_DOT + PM - 1] : 0.0);
+      __syncwarp();
+      ctl_astep(jj + 1, dr);
+      if (lane < NBMAX) sh.cgB[lane] = (lane < sh.n_ghost) ? sh.rba[LY::BA_GH + lane] : 0.0;
+      if (lane == 0) sh.normAu2[(jj + 1) & 1] = sh.rba[LY::BA_W1];
+      __syncwarp();
+      if (t + 1 < p - 1) ctl_coefA(jj + 2);
+    }
+    __syncwarp();
+  }
+
+  // ---- band QR step of column j (control warp; FP64) -------------------------------------------
+  // Input sh.colq (rows j-p..j+p).  Applies the accumulated rotations of the previous 2p columns,
+  // generates the p rotations of column j (pivot row j, zeroing rows j+1..j+p), rotates rows
+  // j..j+p of Shat and of the window, records the direction coefficients, z_j and the squared
+  // residual norms, and sets qstop: 1 = converged at j, 2 = unusable column (error).
+  __device__ __forceinline__ double zval(int j, int c, int k) const {
+    const int P2 = 2 * p, P3 = 3 * p;
+    if (c < P2) {
+      int colid = j + 1 - p + c;
+      if (colid == j + p) return (k == p) ? 1.0 : 0.0;
+      if (k == p) return 0.0;
+      int row = j + k;
+      return sh.P[((row % P3) + P3) % P3][((colid % P2) + P2) % P2];
+    }
+    return sh.Sh[(j + k) % (p + 1)][c - P2];
+  }
+  __device__ __forceinline__ void zput(int j, int c, int k, double v) {
+    const int P2 = 2 * p, P3 = 3 * p;
+    const int row = j + k;
+    if (c < P2)
+      sh.P[((row % P3) + P3) % P3][ring2p(j + 1 - p + c)] = v;
+    else
+      sh.Sh[row % (p + 1)][c - P2] = v;
+  }
+
+  __device__ void qr_warp(int j, int l) {
+    const unsigned long long tq = (blockIdx.x == 0 && lane == 0) ? gtimer() : 0ull;
+    const int P2 = 2 * p, P3 = 3 * p;
+    // 1. y = P col (rows j-2p .. j+p-1), y[3p] = h_{j+p,j}
+    for (int a_ = lane; a_ < P3; a_ += 32) {
+      const int row = j - P2 + a_;
+      const double* Pr = sh.P[((row % P3) + P3) % P3];
+      double s0 = 0.0, s1 = 0.0;
+      int b = 0;
+      for (; b + 1 < P2; b += 2) {
+        s0 += Pr[ring2p(j - p + b)] * sh.colq[b];
+        s1 += Pr[ring2p(j - p + b + 1)] * sh.colq[b + 1];
+      }
+      if (b < P2) s0 += Pr[ring2p(j - p + b)] * sh.colq[b];
+      sh.y[a_] = s0 + s1;
+    }
+    if (lane == 0) sh.y[P3] = sh.colq[P2];
+    __syncwarp();
+    // 2. prefix sums of squares of v = y[2p .. 3p] and the rotations of column j
+    //    (rotation k acts on rows j and j+k: c_k = x_{k-1}/x_k, s_k = v_k/x_k, x_0 = v_0)
+    if (p <= 31) {
+      double v = (lane <= p) ? sh.y[P2 + lane] : 0.0;
+      double s = v * v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        double u = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += u;
+      }
+      if (lane <= p) {
+        sh.pref[lane] = s;
+        sh.rinv[lane] = (s > 0.0) ? rsqrt(s) : 0.0;
+      }
+    } else if (lane == 0) {
+      double s = 0.0;
+      for (int k = 0; k <= p; ++k) {
+        double v = sh.y[P2 + k];
+        s += v * v;
+        sh.pref[k] = s;
+        sh.rinv[k] = (s > 0.0) ? rsqrt(s) : 0.0;
+      }
+    }
+    __syncwarp();
+    for (int k = lane; k <= p; k += 32) {
+      if (k == 0) continue;
+      const double xprev = (k == 1) ? sh.y[P2] : sh.pref[k - 1] * sh.rinv[k - 1];
+      if (sh.pref[k] > 0.0) {
+        sh.gc[k] = xprev * sh.rinv[k];
+        sh.gs[k] = sh.y[P2 + k] * sh.rinv[k];
+      } else {
+        sh.gc[k] = 1.0;
+        sh.gs[k] = 0.0;
+      }
+    }
+    __syncwarp();
+    // 3. rotate the 3p columns (window columns j+1-p .. j+p, then Shat), one lane per column, in
+    //    place: the pivot entry after k rotations is q_k / x_k with q_k = sum_{t<=k} v_t z_t and
+    //    x_k = sqrt(pref_k); row j+k becomes -s_k * pivot_{k-1} + c_k * z_k.
+    for (int a_ = lane; a_ < P2 - 1; a_ += 32) {  // column j+p of the new window: rows j+1-2p..j-1
+      const int row = j + 1 - P2 + a_;
+      sh.P[((row % P3) + P3) % P3][ring2p(j + p)] = 0.0;
+    }
+    for (int c = lane; c < P3; c += 32) {
+      const double z0 = zval(j, c, 0);
+      double q = sh.y[P2] * z0;
+      double piv = z0;
+      for (int k = 1; k <= p; ++k) {
+        const double zk = zval(j, c, k);
+        zput(j, c, k, -sh.gs[k] * piv + sh.gc[k] * zk);
+        q += sh.y[P2 + k] * zk;
+        piv = (sh.pref[k] > 0.0) ? q * sh.rinv[k] : z0;
+      }
+      zput(j, c, 0, piv);
+    }
+    __syncwarp();
+    // 4. direction coefficients of Eq. (search-dir-comp), r_jj, z_j, squared residual norms
+    //    rho_i^2 = ||Shat(j+1:j+p, i)||^2 (Eq. (comp-resid)) and the stopping decision
+    const double rinvp = sh.rinv[p];
+    for (int q = lane; q < 2 * PM; q += 32) {
+      const int qq = q - (2 * PM - P2);  // R row j-2p+qq
+      sh.dirB[l][q] = (qq >= 0 && j - P2 + qq >= 1) ? -sh.y[qq] * rinvp : 0.0;
+    }
+    if (lane == 0) {
+      sh.rjj[l] = sh.pref[p] * rinvp;
+      sh.dirA[l] = sh.sigq * rinvp;
+    }
+    bool conv = true, fin = true;
+    if (lane < p) {
+      sh.Zc[l][lane] = sh.Sh[j % (p + 1)][lane];
+      double s = 0.0;
+      for (int k = 1; k <= p; ++k) {
+        const double v = sh.Sh[(j + k) % (p + 1)][lane];
+        s += v * v;
+      }
+      sh.rho2[lane] = s;
+      conv = (s < sh.thr2[lane]) || sh.inv2[lane] == 0.0;
+      fin = isfinite(s);
+      if (a.rho_hist && blockIdx.x == 0 && j <= a.hist_cap) a.rho_hist[(int64_t)(j - 1) * p + lane] = sqrt(s);
+    }
+    conv = __all_sync(0xffffffffu, conv);
+    fin = __all_sync(0xffffffffu, fin);
+    __syncwarp();
+    if (lane < p) sh.Sh[j % (p + 1)][lane] = 0.0;  // the ring row of j becomes row j+p+1
+    if (lane == 0) {
+      const double rjj = sh.rjj[l];
+      int st = 0;
+      if (!fin || !isfinite(rjj)) {
+        st = 2;
+        sh.qstatus = ST_ERR_NONFINITE;
+      } else if (rjj == 0.0) {
+        st = 2;
+        sh.qstatus = ST_ERR_BREAKDOWN;
+      } else if (conv) {
+        st = 1;
+      }
+      sh.qstop = st;
+      if (blockIdx.x == 0) a.ctl->t_qr += gtimer() - tq;
+    }
+    __syncwarp();
+  }
+
+  // ---- the whole solve ------------------------------------------------------------------------
+  __device__ void run() {
+    const int tid = threadIdx.x;
+    Ctl* ctl = a.ctl;
+    const unsigned long long t_start = gtimer();
+    t_mark = t_start;
+    for (int i = tid; i < (int)(sizeof(Shared<PM>) / 8); i += NT) reinterpret_cast<double*>(&sh)[i] = 0.0;
+    __syncthreads();
+    // the rotation window starts as the identity: P[i][i] = 1 for the columns j-p .. j+p-1 of j = 1
+    for (int c = tid; c < 2 * p; c += NT) {
+      int i = 1 - p + c;
+      sh.P[((i % (3 * p)) + 3 * p) % (3 * p)][ring2p(i)] = 1.0;
+    }
+    __syncthreads();
+    if (!setup_norms()) return fail(t_start);
+    {
+      bool all_zero = true;
+      for (int i = 0; i < p; ++i) all_zero &= (sh.f0n[i] == 0.0);
+      if (all_zero) {
+        if (blockIdx.x == 0 && tid == 0) {
+          ctl->status = ST_OK;
+          ctl->iters = 0;
+          ctl->t_total = gtimer() - t_start;
+        }
+        return;
+      }
+    }
+    // ---- initial QR F0 = U_p S with the dependence test of each column ----
+    for (int i = 0; i < p && sh.status == ST_OK; ++i) {
+      if (!setup_column(i, a.F + (int64_t)i * a.ld, true)) return fail(t_start);
+      double nv2 = sh.red[0];
+      if (!isfinite(nv2)) {
+        set_status(ST_ERR_NONFINITE);
+        break;
+      }
+      const bool dep = !(nv2 > a.gamma * a.gamma * sh.f0n[i] * sh.f0n[i]) || sh.f0n[i] == 0.0;
+      if (dep) {
+        const int bk = sh.bench_next;
+        __syncthreads();
+        if (bk >= a.nbench) {
+          set_status(ST_ERR_BENCH);
+          break;
+        }
+        if (tid == 0) {
+          sh.S[i][i] = 0.0;
+          sh.setup_defl++;
+          sh.bench_next = bk + 1;
+        }
+        __syncthreads();
+        if (!setup_column(i, bench(bk), false)) return fail(t_start);
+        nv2 = sh.red[0];
+        if (!(nv2 > 0.0) || !isfinite(nv2)) {
+          set_status(ST_ERR_BENCH);
+          break;
+        }
+      } else if (tid == 0) {
+        sh.S[i][i] = sqrt(nv2);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        const double s = rsqrt(nv2);
+        sig(i + 1) = s;
+        for (int b = sh.bench_next; b < a.nbench; ++b) sh.bc[b][1][i] = s * s * sh.red[1 + b];
+      }
+      __syncthreads();
+    }
+    if (sh.status != ST_OK) return finish(t_start, 0, 0);
+    if (a.maxit <= 0) return finish(t_start, 0, 3);  // no iteration allowed: X = X0
+    // Shat = [S; 0]: rows 1..p, row p+1 zero (ring index row mod (p+1))
+    for (int t = tid; t < p * p; t += NT) {
+      int r = t / p, c = t % p;
+      sh.Sh[(r + 1) % (p + 1)][c] = sh.S[r][c];
+    }
+    __syncthreads();
+
+    // ---- band iterations, one cycle of p iterations at a time ----
+    int cycle = 1;
+    bool qr_pending = false;  // QR step of the last iteration of the previous cycle not done yet
+    for (;;) {
+      const int j0 = (cycle - 1) * p + 1;
+      if (warp == 0) {
+        if (lane == 0) sh.cycle = cycle;
+        ctl_coefA(j0);
+      }
+      __syncthreads();
+      tick(ctl->t_scalar);
+      if (!pass_spmm(j0, qr_pending ? j0 - 1 : 0, p - 1)) return fail(t_start);
+      if (qr_pending && sh.qstop != 0) {  // the previous cycle ended at its last iteration
+        const int L = (sh.qstop == 1) ? p : p - 1;
+        return end_cycle(t_start, j0 - p, L, cycle - 1, sh.qstop == 1 ? 1 : 2);
+      }
+      if (warp == 0) {  // results of the A step of j0, known coefficients of j0+1
+        const double dr = (lane < p) ? sh.red[LY::SP_DOT + lane] : 0.0;
+        ctl_astep(j0, dr);
+        if (lane < NBMAX) sh.cgB[lane] = (lane < sh.n_ghost) ? sh.red[LY::SP_GH + lane] : 0.0;
+        if (lane == 0) sh.normAu2[j0 & 1] = sh.red[LY::SP_NRM];
+        __syncwarp();
+        if (p > 1) ctl_coefA(j0 + 1);
+      }
+      __syncthreads();
+      if (cycle > 1) pass_dir(j0 - p, p, cycle - 1, true);  // directions of the previous cycle
+      tick(ctl->t_scalar);
+      for (int t = 0; t < p; ++t) {
+        const int jj = j0 + t;
+        const bool hasA = (t < p - 1);
+        if (!pass_ba(jj, t, hasA, t > 0 ? jj - 1 : 0, t - 1)) return fail(t_start);
+        if (t > 0 && sh.qstop != 0)  // iteration jj-1 ended the solve
+          return end_cycle(t_start, j0, sh.qstop == 1 ? t : t - 1, cycle, sh.qstop == 1 ? 1 : 2);
+        // ---- norm of the new vector and dependence test (Sec. 5) ----
+        const double b2 = sh.rba[LY::BA_NRM];
+        if (!isfinite(b2)) {
+          set_status(ST_ERR_NONFINITE);
+          return end_cycle(t_start, j0, t, cycle, 2);
+        }
+        const bool dep = !(b2 > a.gamma * a.gamma * sh.normAu2[jj & 1]);
+        if (dep) {
+          const int bk = sh.bench_next;
+          const int ng0 = sh.n_ghost;
+          __syncthreads();
+          if (bk >= a.nbench) {
+            set_status(ST_ERR_BENCH);
+            return end_cycle(t_start, j0, t, cycle, 2);
+          }
+          // a removed vector is kept only for a near-dependence (||w|| > 1e-12 ||A u_jj||); at the
+          // rounding level of an exact dependence it carries no direction
+          const int newg = (a.ghost && b2 > 1e-24 * sh.normAu2[jj & 1]) ? ng0 : -1;
+          if (tid == 0) {
+            if (newg >= 0) {
+              sh.ghost_born[newg] = jj;
+              sh.n_ghost = newg + 1;
+            }
+            sh.bench_next = bk + 1;
+            sh.deflations++;
+            sh.beta = 0.0;
+          }
+          __syncthreads();
+          if (!substitute(jj, t, hasA, bk, newg)) return fail(t_start);
+          if (sh.status != ST_OK) return end_cycle(t_start, j0, t, cycle, 2);
+        } else if (warp == 0) {
+          if (lane == 0) {
+            const double s = rsqrt(b2);
+            sig(jj + p) = s;
+            sh.beta = b2 * s;
+          }
+          __syncwarp();
+          const double s = sig(jj + p);
+          for (int b = sh.bench_next + lane; b < a.nbench; b += 32)
+            sh.bc[b][(cycle + 1) & 1][t] = s * s * sh.rba[LY::BA_BEN + b];
+          for (int k = 1 + lane; k < p; k += 32)
+            sh.gram[ring2p(jj + p)][p - k - 1] = s * sig(jj + k) * sh.rba[LY::BA_GR + k - 1];
+        }
+        __syncthreads();
+        if (warp == 0) ctl_after_ba(jj, t, hasA);
+        __syncthreads();
+        tick(ctl->t_scalar);
+        if (jj >= a.maxit) {  // last permitted iteration: finish its QR step now
+          if (warp == 0) qr_warp(jj, t);
+          __syncthreads();
+          const int L = (sh.qstop == 2) ? t : t + 1;
+          return end_cycle(t_start, j0, L, cycle, sh.qstop == 2 ? 2 : (sh.qstop == 1 ? 1 : 3));
+        }
+      }
+      qr_pending = true;
+      ++cycle;
+    }
+  }
+
+  // directions and iterate for the L completed iterations of cycle `cyc` starting at j0; stop:
+  // 1 converged, 2 error, 3 iteration limit
+  __device__ void end_cycle(unsigned long long t_start, int j0, int L, int cyc, int stop) {
+    if (L > 0) pass_dir(j0, L, cyc, false);
+    finish(t_start, j0 + L - 1, stop);
+  }
+
+  __device__ void finish(unsigned long long t_start, int iters, int stop) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      Ctl* ctl = a.ctl;
+      int st = sh.status;
+      if (st == ST_OK && stop == 2) st = sh.qstatus != 0 ? sh.qstatus : ST_ERR_NONFINITE;
+      if (st == ST_OK) st = (stop == 1) ? ST_OK : ST_NOT_CONVERGED;
+      ctl->status = st;
+      ctl->iters = iters;
+      ctl->cycles = iters > 0 ? (iters + p - 1) / p : 0;
+      ctl->deflations = sh.deflations;
+      ctl->setup_deflations = sh.setup_defl;
+      ctl->bench_used = sh.bench_next;
+      double worst = 0.0;
+      for (int i = 0; i < p; ++i) worst = fmax(worst, sh.rho2[i] * sh.inv2[i]);
+      ctl->relres_est_max = sqrt(worst);
+      ctl->t_total = gtimer() - t_start;
+    }
+  }
+  __device__ void fail(unsigned long long t_start) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.ctl->status = ST_ERR_TIMEOUT;
+      a.ctl->t_total = gtimer() - t_start;
+    }
+  }
+};
+
+template <typename V, int PM, int NT>
+constexpr size_t solve_smem_bytes() {
+  return ((sizeof(Shared<PM>) + 15) / 16) * 16 + sizeof(V) * (size_t)16 * (NT - 32);
+}
+
+template <typename V, int PM, int NT>
+__global__ void __launch_bounds__(NT, 1) bminres_solve_kernel(SolveArgs<V> args) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Shared<PM>& sh = *reinterpret_cast<Shared<PM>*>(smem_raw);
+  V* scr = reinterpret_cast<V*>(smem_raw + ((sizeof(Shared<PM>) + 15) / 16) * 16);
+  Engine<V, PM, NT> e(args, sh, scr);
+  e.run();
+}
+
+}  // namespace bmr
