@@ -49,7 +49,8 @@ typedef struct {
                         product and orthogonalisation inside an FP64 iterative-refinement loop;
                         the residual B - A X, coefficients, band QR and dependence test in FP64 */
   double gamma;      /* dependence tolerance, relative: a new vector is dependent when its norm
-                        after orthogonalisation is <= gamma * ||A u_j|| (Sec. 5).  Default 1e-8 */
+                        after orthogonalisation is <= gamma * ||A u_j|| (Sec. 5).  Default 1e-8;
+                        FP32 inner solves (MIXED) use max(gamma, 1e-5) */
   int bench;         /* size of the dynamic substitutes bench (Sec. 5.1), 0..8.  Default 4 */
   uint64_t seed;     /* seed of the counter-based SplitMix64 stream for bench vectors */
   int ghost;         /* 1: keep a removed vector and orthogonalise against it for the next 2p
@@ -73,12 +74,14 @@ typedef struct {
                             (Eq. (comp-resid)); in MIXED mode, of the last inner solve */
   double relres_true_max;/* max_i ||b_i - A x_i|| / ||b_i - A x0_i||, recomputed in FP64 */
   double device_ms;      /* device time from the first to the last kernel of the solve */
-  double stream_ms;      /* timeline of the persistent kernel's block 0 (summed over inner solves):
-                            streaming passes over the vectors, */
+  double kernel_ms;      /* CUDA-event time of the persistent solve kernel launches (summed) */
+  double stream_ms;      /* timeline of the persistent kernel's block 0 (global timer, summed over
+                            launches): streaming passes over the vectors, */
   double reduce_ms;      /* grid reductions including barriers, */
-  double scalar_ms;      /* band QR and coefficient bookkeeping, */
-  double kernel_ms;      /* and the whole persistent kernel; */
-  double qr_ms;          /* band QR steps, run by a control warp during the streaming passes */
+  double scalar_ms;      /* coefficient bookkeeping between passes, */
+  double timeline_ms;    /* the whole kernel, */
+  double qr_ms;          /* and the band QR steps of the control warp (overlapped with streaming) */
+  int launches;          /* kernels launched by this call */
 } bminres_info;
 
 /* Fill *opts with the defaults listed above. */

@@ -31,8 +31,9 @@ class Info(ctypes.Structure):
                 ("outer", ctypes.c_int), ("deflations", ctypes.c_int), ("setup_deflations", ctypes.c_int),
                 ("bench_used", ctypes.c_int), ("grid_blocks", ctypes.c_int), ("relres_est_max", ctypes.c_double),
                 ("relres_true_max", ctypes.c_double), ("device_ms", ctypes.c_double),
-                ("stream_ms", ctypes.c_double), ("reduce_ms", ctypes.c_double), ("scalar_ms", ctypes.c_double),
-                ("kernel_ms", ctypes.c_double), ("qr_ms", ctypes.c_double)]
+                ("kernel_ms", ctypes.c_double), ("stream_ms", ctypes.c_double), ("reduce_ms", ctypes.c_double),
+                ("scalar_ms", ctypes.c_double), ("timeline_ms", ctypes.c_double), ("qr_ms", ctypes.c_double),
+                ("launches", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -54,7 +54,8 @@ struct bminres_handle_s {
   bmr::Ctl* ctl_host = nullptr; // pinned
   double* norms_host = nullptr; // pinned, 2 * 32
   bmr::Workspace ws;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk0 = nullptr, evk1 = nullptr;
+  int launches = 0;  // kernels launched by the current call
   int hist_cap = 0;
   double* hist = nullptr;  // device, hist_cap * 32
   int hist_count = 0, hist_p = 0;
@@ -218,6 +219,7 @@ bminres_status residual(bminres_handle h, int p, const double* B, const double* 
   BMR_TRY(cudaGetLastError());
   bmr::finish_norms_kernel<<<1, bmr::AUX_NT, 0, s>>>(p, nres, w.npart, w.norms);
   BMR_TRY(cudaGetLastError());
+  h->launches += (nres > 0) ? 2 : 1;
   if (norms_to_host) {
     BMR_TRY(cudaMemcpyAsync(h->norms_host, w.norms, sizeof(double) * p, cudaMemcpyDeviceToHost, s));
     BMR_TRY(cudaStreamSynchronize(s));
@@ -226,9 +228,16 @@ bminres_status residual(bminres_handle h, int p, const double* B, const double* 
 }
 
 // One persistent solve on F (vectors of type V), updating Xout (row-major n x p of type V).
+// Dependence threshold for a vector precision: FP32 Gram-Schmidt leaves ~1e-7 of an exactly
+// dependent vector, so an FP32 inner solve cannot resolve gamma below ~1e-5.
+template <typename V>
+double effective_gamma(double gamma) {
+  return sizeof(V) == sizeof(float) ? std::max(gamma, 1e-5) : gamma;
+}
+
 template <typename V>
 bminres_status persistent_solve(bminres_handle h, int p, V* Xout, double tol, int maxit, cudaStream_t s,
-                                const V* vals, Ctl* result) {
+                                const V* vals, Ctl* result, double* kernel_ms) {
   bmr::Workspace& w = h->ws;
   const int64_t ld = padded_ld(h->n);
   const size_t es = sizeof(V);
@@ -246,7 +255,7 @@ bminres_status persistent_solve(bminres_handle h, int p, V* Xout, double tol, in
   a.ghost = h->opts.ghost;
   a.maxit = maxit;
   a.tol = tol;
-  a.gamma = h->opts.gamma;
+  a.gamma = effective_gamma<V>(h->opts.gamma);
   a.seed = h->opts.seed;
   a.rowptr = h->rowptr;
   a.colidx = h->colidx;
@@ -263,9 +272,14 @@ bminres_status persistent_solve(bminres_handle h, int p, V* Xout, double tol, in
   a.rho_hist = h->hist;
   a.hist_cap = h->hist_cap;
   a.barrier_limit_ns = BARRIER_LIMIT_NS;
+  BMR_TRY(cudaEventRecord(h->evk0, s));
   BMR_TRY(launch_solve<V>(pm_for(p), a, w.grid, s));
+  BMR_TRY(cudaEventRecord(h->evk1, s));
+  h->launches++;
   BMR_TRY(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
   BMR_TRY(cudaStreamSynchronize(s));
+  float kms = 0.f;
+  if (cudaEventElapsedTime(&kms, h->evk0, h->evk1) == cudaSuccess) *kernel_ms += kms;
   *result = *h->ctl_host;
   h->hist_count = std::min(result->iters, h->hist_cap);
   h->hist_p = p;
@@ -276,7 +290,7 @@ void add_timeline(bminres_info& inf, const Ctl& r) {
   inf.stream_ms += r.t_stream * 1e-6;
   inf.reduce_ms += r.t_reduce * 1e-6;
   inf.scalar_ms += r.t_scalar * 1e-6;
-  inf.kernel_ms += r.t_total * 1e-6;
+  inf.timeline_ms += r.t_total * 1e-6;
   inf.qr_ms += r.t_qr * 1e-6;
 }
 
@@ -297,6 +311,7 @@ bminres_status solve_device(bminres_handle h, int p, const double* B, double* X,
                             cudaStream_t s, double* relres_true, bminres_info* info) {
   bminres_info inf;
   memset(&inf, 0, sizeof(inf));
+  h->launches = 0;
   const bool mixed = (h->opts.precision == BMINRES_MIXED);
   bminres_status st = ensure_ws(h, p, mixed ? 1 : 0);
   if (st != BMINRES_OK) return st;
@@ -309,7 +324,7 @@ bminres_status solve_device(bminres_handle h, int p, const double* B, double* X,
     if (st != BMINRES_OK) return st;
     for (int i = 0; i < p; ++i) f0[i] = h->norms_host[i];
     Ctl r;
-    st = persistent_solve<double>(h, p, X, tol, maxit, s, h->vals, &r);
+    st = persistent_solve<double>(h, p, X, tol, maxit, s, h->vals, &r, &inf.kernel_ms);
     if (st != BMINRES_OK) return st;
     inf.iters = r.iters;
     inf.cycles = r.cycles;
@@ -339,7 +354,7 @@ bminres_status solve_device(bminres_handle h, int p, const double* B, double* X,
       }
       if (used >= maxit) break;
       Ctl r;
-      rs = persistent_solve<float>(h, p, w.D, h->opts.tol_inner, maxit - used, s, h->vals32, &r);
+      rs = persistent_solve<float>(h, p, w.D, h->opts.tol_inner, maxit - used, s, h->vals32, &r, &inf.kernel_ms);
       if (rs != BMINRES_OK) return rs;
       used += r.iters;
       inf.iters += r.iters;
@@ -359,6 +374,7 @@ bminres_status solve_device(bminres_handle h, int p, const double* B, double* X,
       bmr::add_correction_kernel<<<std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4096)), 256, 0, s>>>(
           total, X, w.D);
       BMR_TRY(cudaGetLastError());
+      h->launches++;
       if (r.iters == 0) break;  // inner solve could not make progress
     }
   }
@@ -381,6 +397,7 @@ bminres_status solve_device(bminres_handle h, int p, const double* B, double* X,
   float ms = 0.f;
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   inf.device_ms = ms;
+  inf.launches = h->launches;
   inf.status = st;
   if (info) *info = inf;
   return st;
@@ -478,7 +495,9 @@ bminres_status bminres_create(bminres_handle* out, int64_t n, int64_t nnz, const
   if (cudaMalloc(&h->ctl, sizeof(Ctl)) != cudaSuccess) return fail(BMINRES_ERR_OOM);
   if (cudaMallocHost(&h->ctl_host, sizeof(Ctl)) != cudaSuccess) return fail(BMINRES_ERR_OOM);
   if (cudaMallocHost(&h->norms_host, sizeof(double) * 64) != cudaSuccess) return fail(BMINRES_ERR_OOM);
-  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) return fail(BMINRES_ERR_CUDA);
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
+      cudaEventCreate(&h->evk0) != cudaSuccess || cudaEventCreate(&h->evk1) != cudaSuccess)
+    return fail(BMINRES_ERR_CUDA);
   if (cudaMemcpy(h->rowptr, rp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(BMINRES_ERR_CUDA);
   if (nnz > 0 && cudaMemcpy(h->colidx, ci.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -520,6 +539,8 @@ void bminres_destroy(bminres_handle h) {
   if (h->norms_host) cudaFreeHost(h->norms_host);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->evk0) cudaEventDestroy(h->evk0);
+  if (h->evk1) cudaEventDestroy(h->evk1);
   if (h->hist) cudaFree(h->hist);
   delete h;
 }
