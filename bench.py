@@ -301,6 +301,22 @@ def run_ours(args):
     return 0
 
 
+def run_profile_case(args):
+    """Profiling aid (not a benchmark result): one solve of the workload capped at
+    --profile-iters band iterations, for ncu captures of the persistent kernel."""
+    import torch
+
+    from paper_1301_2102_gb300 import Solver
+
+    A, B = workload(args.grid)
+    Bd = torch.from_numpy(B).cuda()
+    with Solver(A, precision="fp64" if args.mode == "both" else args.mode, bench=4) as s:
+        X, info, rel = s.solve(Bd, tol=TOL, maxit=args.profile_iters)
+        torch.cuda.synchronize()
+    print(json.dumps({"profile_case": True, "grid": args.grid, "mode": args.mode, **info}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -312,7 +328,11 @@ def main():
     ap.add_argument("--grid", type=int, default=128)
     ap.add_argument("--cpu-sample-iters", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="profiling aid: run one solve capped at this many band iterations and print its info")
     args = ap.parse_args()
+    if args.profile_iters > 0:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
