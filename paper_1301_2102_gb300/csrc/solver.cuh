@@ -115,6 +115,9 @@ struct __align__(16) Shared {
     double S[PM][PM];           // initial QR factor
   };
   double qd[PM], qe[PM];        // set-up Gram-Schmidt coefficients
+  // single-precision copies of the direction-pass coefficients (used by FP32 vectors, so that the
+  // row loop does no double -> float conversions, which run on the slow FP64 pipe)
+  float dirAf[PM], dirBf[PM][2 * PM], Zcf[PM][PM], bcf[NBMAX][2][PM];
   double red[Layout<PM>::NVMAX];   // values of the last grid reduction
   double rba[Layout<PM>::NVMAX];   // saved values of the last fused pass
   double s2[Layout<PM>::NVMAX][32];
@@ -643,7 +646,7 @@ struct Engine {
       } else {
         double s = rsqrt(nr2);
         sig(j + p) = s;
-        for (int b = bk + 1; b < a.nbench; ++b) sh.bc[b][(cyc + 1) & 1][t] = s * s * sh.red[LY::D2_BEN + b];
+        for (int b = bk + 1; b < a.nbench; ++b) set_bc(b, (cyc + 1) & 1, t, s * s * sh.red[LY::D2_BEN + b]);
         for (int k = 1; k < p; ++k) sh.gram[ring2p(j + p)][p - k - 1] = s * sig(j + k) * sh.red[LY::D2_GR + k - 1];
       }
     }
@@ -672,6 +675,23 @@ struct Engine {
   // m_j = (u_j - sum_{i=j-2p}^{j-1} r_{i,j} m_i) / r_{j,j}   (Eq. (search-dir-comp))
   // X  += sum_l m_{j0+l} z_{j0+l}^T                           (Eq. (approx-update), blocked)
   // bench vectors lose their components along u_{j0} .. u_{j0+p-1} (coefficients of parity cyc).
+  __device__ __forceinline__ void set_bc(int b, int par, int l, double v) {
+    sh.bc[b][par][l] = v;
+    sh.bcf[b][par][l] = (float)v;
+  }
+  __device__ __forceinline__ A cdirA(int l) const {
+    if constexpr (sizeof(A) == 4) return sh.dirAf[l]; else return sh.dirA[l];
+  }
+  __device__ __forceinline__ A cdirB(int l, int q) const {
+    if constexpr (sizeof(A) == 4) return sh.dirBf[l][q]; else return sh.dirB[l][q];
+  }
+  __device__ __forceinline__ A cZ(int l, int c) const {
+    if constexpr (sizeof(A) == 4) return sh.Zcf[l][c]; else return sh.Zc[l][c];
+  }
+  __device__ __forceinline__ A cbc(int b, int par, int l) const {
+    if constexpr (sizeof(A) == 4) return sh.bcf[b][par][l]; else return sh.bc[b][par][l];
+  }
+
   __device__ void pass_dir(int j0, int L, int cyc, bool update_bench) {
     if (warp > 0) {
       const int nb = a.nbench, b0 = sh.bench_next;
@@ -693,9 +713,9 @@ struct Engine {
 #pragma unroll
         for (int l = 0; l < PM; ++l) {
           if (l < L) {
-            A m = (A)sh.dirA[l] * uv[l];
+            A m = cdirA(l) * uv[l];
 #pragma unroll
-            for (int q = 0; q < 2 * PM; ++q) m += (A)sh.dirB[l][q] * mw[l + q];
+            for (int q = 0; q < 2 * PM; ++q) m += cdirB(l, q) * mw[l + q];
             mw[2 * PM + l] = m;
             mslot(j0 + l)[r] = (V)m;
           } else {
@@ -709,7 +729,7 @@ struct Engine {
             A s = xr[c];
 #pragma unroll
             for (int l = 0; l < PM; ++l)
-              if (l < L) s += mw[2 * PM + l] * (A)sh.Zc[l][c];
+              if (l < L) s += mw[2 * PM + l] * cZ(l, c);
             xr[c] = (V)s;
           }
         if (update_bench) {
@@ -719,7 +739,7 @@ struct Engine {
               A v = bench(b)[r];
 #pragma unroll
               for (int l = 0; l < PM; ++l)
-                if (l < p) v -= (A)sh.bc[b][cyc & 1][l] * uv[l];
+                if (l < p) v -= cbc(b, cyc & 1, l) * uv[l];
               bench(b)[r] = (V)v;
             }
         }
@@ -901,15 +921,19 @@ struct Engine {
     const double rinvp = sh.rinv[p];
     for (int q = lane; q < 2 * PM; q += 32) {
       const int qq = q - (2 * PM - P2);  // R row j-2p+qq
-      sh.dirB[l][q] = (qq >= 0 && j - P2 + qq >= 1) ? -sh.y[qq] * rinvp : 0.0;
+      const double dbq = (qq >= 0 && j - P2 + qq >= 1) ? -sh.y[qq] * rinvp : 0.0;
+      sh.dirB[l][q] = dbq;
+      sh.dirBf[l][q] = (float)dbq;
     }
     if (lane == 0) {
       sh.rjj[l] = sh.pref[p] * rinvp;
       sh.dirA[l] = sh.sigq * rinvp;
+      sh.dirAf[l] = (float)sh.dirA[l];
     }
     bool conv = true, fin = true;
     if (lane < p) {
       sh.Zc[l][lane] = sh.Sh[j % (p + 1)][lane];
+      sh.Zcf[l][lane] = (float)sh.Zc[l][lane];
       double s = 0.0;
       for (int k = 1; k <= p; ++k) {
         const double v = sh.Sh[(j + k) % (p + 1)][lane];
@@ -1004,7 +1028,7 @@ struct Engine {
       if (tid == 0) {
         const double s = rsqrt(nv2);
         sig(i + 1) = s;
-        for (int b = sh.bench_next; b < a.nbench; ++b) sh.bc[b][1][i] = s * s * sh.red[1 + b];
+        for (int b = sh.bench_next; b < a.nbench; ++b) set_bc(b, 1, i, s * s * sh.red[1 + b]);
       }
       __syncthreads();
     }
@@ -1089,7 +1113,7 @@ struct Engine {
           __syncwarp();
           const double s = sig(jj + p);
           for (int b = sh.bench_next + lane; b < a.nbench; b += 32)
-            sh.bc[b][(cycle + 1) & 1][t] = s * s * sh.rba[LY::BA_BEN + b];
+            set_bc(b, (cycle + 1) & 1, t, s * s * sh.rba[LY::BA_BEN + b]);
           for (int k = 1 + lane; k < p; k += 32)
             sh.gram[ring2p(jj + p)][p - k - 1] = s * sig(jj + k) * sh.rba[LY::BA_GR + k - 1];
         }
