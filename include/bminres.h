@@ -130,6 +130,34 @@ bminres_status bminres_get_history(bminres_handle handle, double* out, int* coun
 /* Y = A X for an n x p block (FP64, CSR summation order).  1 <= p <= 32. */
 bminres_status bminres_spmm(bminres_handle handle, int p, const double* X, double* Y, bminres_stream stream);
 
+/* Size of the static device scratch array used by bminres_solve_noalloc (64 MiB).  Every GPU on
+ * which the library is loaded holds this array until the process exits. */
+#define BMINRES_NOALLOC_SCRATCH_BYTES (64ull << 20)
+
+/* FP64 solve of A X = B that allocates nothing (the paper has no counterpart; this is a service
+ * entry point of the library).  It is meant for callers that must not call cudaMalloc: code whose
+ * device memory is owned by another framework's pool (a raw cudaMalloc there fragments the pool or
+ * exceeds its budget), and latency-critical loops that cannot accept the implicit device-wide
+ * synchronisation of cudaMalloc / cudaFree.  The result is the same as bminres_create +
+ * bminres_solve in FP64 mode with the default options (or *opts, whose precision must be FP64).
+ *  - rowptr, colidx, vals (CSR of A, int32 indices, full symmetric pattern), B and X (row-major
+ *    n x p; X in: X0, out: X) must be device pointers; the caller owns them.  The CSR is not
+ *    validated beyond n >= 0 and 0 <= nnz < 2^31.
+ *  - All workspace lives in one static device array of BMINRES_NOALLOC_SCRATCH_BYTES; the call
+ *    fits when (6 p + 2 bench) * 8 * round_up(n, 64) bytes plus ~1 MiB do not exceed it (about
+ *    n <= 140,000 at p = 8 with 4 bench vectors); larger problems are rejected with
+ *    BMINRES_ERR_INVALID before any device work.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *    that device current; make that first call before any stream capture.
+ *  - Every call shares the array and it keeps the last call's contents: calls that overlap on the
+ *    GPU (other streams, other host threads) race and must not be issued.
+ *  - relres_true (host, p doubles) and info may be NULL; info->device_ms is 0 (no event is
+ *    created); info->timeline_ms carries the kernel's own device timer. */
+bminres_status bminres_solve_noalloc(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colidx,
+                                     const double* vals, int p, const double* B, double* X, double tol,
+                                     int maxit, const bminres_opts* opts, bminres_stream stream,
+                                     double* relres_true, bminres_info* info);
+
 /* Release the handle and everything it owns.  NULL is ignored. */
 void bminres_destroy(bminres_handle handle);
 

@@ -1,5 +1,6 @@
 // Non-persistent kernels around the solve: residual R = B - A X (FP64) written as column vectors,
-// the block product Y = A X, the sampled outer product for the adjoint, and X += D.
+// the block product Y = A X, the sampled outer product for the adjoint, and X += D.  Defined in
+// this header with internal linkage so that each translation unit that launches them has its own.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(AUX_NT) residual_kernel(int64_t n, int p, cons
 }
 
 // out[c] = sqrt(sum_b part[c][b]) for c < p (one block, fixed order).
-__global__ void finish_norms_kernel(int p, int nparts, const double* part, double* out) {
+static __global__ void finish_norms_kernel(int p, int nparts, const double* part, double* out) {
   __shared__ double red[AUX_NT];
   for (int c = 0; c < p; ++c) {
     double s = 0.0;
@@ -76,7 +77,7 @@ __global__ void finish_norms_kernel(int p, int nparts, const double* part, doubl
 }
 
 // Y = A X for row-major n x p blocks, FP64, CSR summation order.
-__global__ void __launch_bounds__(AUX_NT) spmm_kernel(int64_t n, int p, const int32_t* __restrict__ rowptr,
+static __global__ void __launch_bounds__(AUX_NT) spmm_kernel(int64_t n, int p, const int32_t* __restrict__ rowptr,
                                                       const int32_t* __restrict__ colidx,
                                                       const double* __restrict__ vals, const double* X, double* Y) {
   const int64_t r = (int64_t)blockIdx.x * AUX_NT + threadIdx.x;
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(AUX_NT) spmm_kernel(int64_t n, int p, const in
 }
 
 // dA[k] = -sum_c L[row_k, c] * X[col_k, c] for every stored entry k (row-major n x p L and X).
-__global__ void __launch_bounds__(AUX_NT) sddmm_kernel(int64_t n, int p, const int32_t* __restrict__ rowptr,
+static __global__ void __launch_bounds__(AUX_NT) sddmm_kernel(int64_t n, int p, const int32_t* __restrict__ rowptr,
                                                        const int32_t* __restrict__ colidx, const double* Lm,
                                                        const double* X, double* dA) {
   const int64_t r = (int64_t)blockIdx.x * AUX_NT + threadIdx.x;
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(AUX_NT) sddmm_kernel(int64_t n, int p, const i
 }
 
 // X += D (FP64 += FP32), row-major n x p, and D = 0.
-__global__ void add_correction_kernel(int64_t total, double* X, float* D) {
+static __global__ void add_correction_kernel(int64_t total, double* X, float* D) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     X[i] += (double)D[i];
     D[i] = 0.0f;
@@ -123,7 +124,7 @@ __global__ void add_correction_kernel(int64_t total, double* X, float* D) {
 }
 
 // FP32 copy of the matrix values.
-__global__ void to_float_kernel(int64_t total, const double* a, float* b) {
+static __global__ void to_float_kernel(int64_t total, const double* a, float* b) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = (float)a[i];
 }
