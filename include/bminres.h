@@ -82,6 +82,8 @@ typedef struct {
   double timeline_ms;    /* the whole kernel, */
   double qr_ms;          /* and the band QR steps of the control warp (overlapped with streaming) */
   int launches;          /* kernels launched by this call */
+  double spmm_ms;        /* part of stream_ms: block-product passes (SpMM fused with an A step) */
+  double dir_ms;         /* part of stream_ms: direction and iterate passes */
 } bminres_info;
 
 /* Fill *opts with the defaults listed above. */

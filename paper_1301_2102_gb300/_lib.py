@@ -33,7 +33,7 @@ class Info(ctypes.Structure):
                 ("relres_true_max", ctypes.c_double), ("device_ms", ctypes.c_double),
                 ("kernel_ms", ctypes.c_double), ("stream_ms", ctypes.c_double), ("reduce_ms", ctypes.c_double),
                 ("scalar_ms", ctypes.c_double), ("timeline_ms", ctypes.c_double), ("qr_ms", ctypes.c_double),
-                ("launches", ctypes.c_int)]
+                ("launches", ctypes.c_int), ("spmm_ms", ctypes.c_double), ("dir_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -287,7 +287,9 @@ bminres_status persistent_solve(bminres_handle h, int p, V* Xout, double tol, in
 }
 
 void add_timeline(bminres_info& inf, const Ctl& r) {
-  inf.stream_ms += r.t_stream * 1e-6;
+  inf.stream_ms += (r.t_stream + r.t_sp + r.t_dir) * 1e-6;
+  inf.spmm_ms += r.t_sp * 1e-6;
+  inf.dir_ms += r.t_dir * 1e-6;
   inf.reduce_ms += r.t_reduce * 1e-6;
   inf.scalar_ms += r.t_scalar * 1e-6;
   inf.timeline_ms += r.t_total * 1e-6;

@@ -242,7 +242,9 @@ extern "C" bminres_status bminres_solve_noalloc(int64_t n, int64_t nnz, const in
     info->grid_blocks = grid;
     info->relres_est_max = r.relres_est_max;
     info->relres_true_max = worst;
-    info->stream_ms = r.t_stream * 1e-6;
+    info->stream_ms = (r.t_stream + r.t_sp + r.t_dir) * 1e-6;
+    info->spmm_ms = r.t_sp * 1e-6;
+    info->dir_ms = r.t_dir * 1e-6;
     info->reduce_ms = r.t_reduce * 1e-6;
     info->scalar_ms = r.t_scalar * 1e-6;
     info->timeline_ms = r.t_total * 1e-6;

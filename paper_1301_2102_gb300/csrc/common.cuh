@@ -35,6 +35,7 @@ struct Ctl {
   // scalar work (band QR and coefficient bookkeeping)
   unsigned long long t_stream, t_reduce, t_scalar, t_total;
   unsigned long long t_qr;  // band QR steps of the control warp (overlapped with streaming)
+  unsigned long long t_sp, t_dir;  // block-product and direction passes (t_stream: the fused passes)
 };
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -92,6 +93,53 @@ __device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks, unsigne
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// ---- bulk copies global -> shared completed on an mbarrier (PTX: cp.async.bulk, mbarrier) -------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// make initialised mbarriers visible to the async proxy
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// order this thread's earlier generic-proxy accesses before its later async-proxy (bulk) accesses
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+// the single arrival of a phase, announcing `bytes` of bulk copies that complete on it
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait until the phase with the given parity has completed; gives up after limit_ns.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned long long limit_ns) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  while (!mbar_test(bar, parity))
+    if (gtimer() - t0 > limit_ns) return false;
+  return true;
+}
+// bytes (a multiple of 16) from 16-byte aligned global src to 16-byte aligned shared dst
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// named barrier `id` over `count` threads (a multiple of 32)
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) used counter-style: value t of the stream with

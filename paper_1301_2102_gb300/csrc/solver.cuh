@@ -82,8 +82,21 @@ struct Layout {
   static constexpr int NVMAX = (2 * PM + NBMAX > BA_N) ? 2 * PM + NBMAX : BA_N;
 };
 
+constexpr int NSTAGE_MAX = 2;  // staging buffers of the streaming passes (fewer for p > 16)
+constexpr int TQMAX = 512;  // tiles per block whose CSR offsets are tabulated for the block product
+
 template <int PM>
 struct __align__(16) Shared {
+  unsigned long long tbar[NSTAGE_MAX];  // completion barriers of the staging buffers
+  int tq[TQMAX + 1];                // rowptr at the block-product tile boundaries of this block
+  int tq_n;                         // tiles tabulated (-1: too many, CSR read directly)
+  int csr_nnz;                      // rowptr[n]
+  // vectors staged by the current streaming pass: global address of row 0 and byte offset of
+  // the slot in a staging buffer (written and read by the issuing warp only)
+  const char* cp_src[3 * PM + 8];
+  unsigned cp_dst[3 * PM + 8];
+  int cp_n, cp_pad;
+  int terr, pad_t;                  // a staging wait ran out in this block
   int cycle, status, qstop, qstatus;
   int bench_next, n_ghost, deflations, setup_defl;
   int ghost_born[NBMAX];
@@ -124,6 +137,116 @@ struct __align__(16) Shared {
   double d4[Layout<PM>::NVMAX][4];
 };
 
+// ---- G consecutive elements of a vector in one access (G * sizeof(V) <= 16 bytes, aligned) ----
+template <int G>
+struct IC {
+  static constexpr int value = G;
+};
+
+template <int G, typename V>
+__device__ __forceinline__ void vld(const V* p, V (&x)[G]) {
+  static_assert(G == 1 || G == 2 || G == 4, "group width");
+  static_assert(G * sizeof(V) <= 16, "group wider than 16 bytes");
+  if constexpr (G == 1) {
+    x[0] = *p;
+  } else if constexpr (sizeof(V) == 8) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    x[0] = t.x;
+    x[1] = t.y;
+  } else if constexpr (G == 2) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    x[0] = t.x;
+    x[1] = t.y;
+  } else {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    x[0] = t.x;
+    x[1] = t.y;
+    x[2] = t.z;
+    x[3] = t.w;
+  }
+}
+
+template <int G, typename V>
+__device__ __forceinline__ void vst(V* p, const V (&x)[G]) {
+  if constexpr (G == 1) {
+    *p = x[0];
+  } else if constexpr (sizeof(V) == 8) {
+    *reinterpret_cast<double2*>(p) = make_double2(x[0], x[1]);
+  } else if constexpr (G == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(x[0], x[1]);
+  } else {
+    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+  }
+}
+
+// G consecutive elements from shared memory (16/8/4-byte aligned).  Volatile, so that a value the
+// code reads twice is re-read from shared memory instead of being held in registers across a row.
+template <int G>
+__device__ __forceinline__ void sld(const float* p, float (&x)[G]) {
+  const unsigned a = smem_u32(p);
+  if constexpr (G == 1) {
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(x[0]) : "r"(a));
+  } else if constexpr (G == 2) {
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(x[0]), "=f"(x[1]) : "r"(a));
+  } else {
+    static_assert(G == 4, "group width");
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]) : "r"(a));
+  }
+}
+template <int G>
+__device__ __forceinline__ void sld(const double* p, double (&x)[G]) {
+  const unsigned a = smem_u32(p);
+  if constexpr (G == 1) {
+    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(x[0]) : "r"(a));
+  } else {
+    static_assert(G == 2, "group width");
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x[0]), "=d"(x[1]) : "r"(a));
+  }
+}
+
+// Shared-memory staging of the streaming passes: NSTAGE buffers of STG bytes after the Shared block
+// (the reduction scratch reuses them).  A pass that streams `nsl` vector slots per row works on
+// tiles of rows(nsl) rows; its consumers take groups of group(nsl) consecutive rows.
+template <typename V, int PM, int NT>
+struct Tiles {
+  static constexpr int NS = NT - 32;
+  static constexpr int NSTAGE = PM > 16 ? 2 : NSTAGE_MAX;
+  static constexpr size_t SH = (sizeof(Shared<PM>) + 127) / 128 * 128;
+  static constexpr size_t BUDGET = 227 * 1024 - 1024;  // dynamic shared memory of one block
+  static constexpr size_t STG_MAX = 80 * 1024;
+  static constexpr size_t STG =
+      ((BUDGET - SH) / NSTAGE < STG_MAX ? (BUDGET - SH) / NSTAGE : STG_MAX) / 128 * 128;
+  __host__ __device__ static constexpr int cap(int nsl) { return (int)(STG / ((size_t)nsl * sizeof(V))); }
+  __host__ __device__ static constexpr int group(int nsl) {
+    int g = 16 / (int)sizeof(V);
+    while (g > 1 && NS * g > cap(nsl)) g /= 2;
+    return g;
+  }
+  __host__ __device__ static constexpr int rows(int nsl) {
+    return cap(nsl) >= NS * group(nsl) ? cap(nsl) / (NS * group(nsl)) * (NS * group(nsl)) : cap(nsl) / 32 * 32;
+  }
+  __host__ __device__ static constexpr size_t smem_bytes() { return SH + NSTAGE * STG; }
+  // block product: rows per tile and group width, with the tile's CSR segment staged beside the
+  // 2p vector slots (up to 8 nonzeros per row on average)
+  __host__ __device__ static constexpr size_t sp_bytes(int t) {
+    return ((size_t)2 * PM * t * sizeof(V) + (size_t)(t + 4) * 4 + 15) / 16 * 16 +
+           ((size_t)8 * t * 4 + 15) / 16 * 16 + (size_t)8 * t * sizeof(V);
+  }
+  __host__ __device__ static constexpr int sp_group() {
+    int g = 16 / (int)sizeof(V);
+    while (g > 1 && sp_bytes(NS * g) > STG) g /= 2;
+    return g;
+  }
+  __host__ __device__ static constexpr int sp_rows() {
+    int t = NS * sp_group();
+    if (sp_bytes(t) > STG) {
+      t = 32;
+      while (sp_bytes(t + 32) <= STG) t += 32;
+    }
+    return t;
+  }
+};
+
 template <typename V, int PM, int NT>
 struct Engine {
   using A = V;  // per-thread accumulation in the vector precision
@@ -131,9 +254,13 @@ struct Engine {
   static constexpr int NVMAX = LY::NVMAX;
   static constexpr int NS = NT - 32;  // streaming threads (warps 1..NT/32-1)
   static constexpr int RCH = 16;      // values per chunk of a block reduction
+  static constexpr int NBPRE = 4;     // bench vectors held in registers by the fused pass
   const SolveArgs<V>& a;
   Shared<PM>& sh;
-  A* scr;  // [RCH][NS] scratch for block reductions
+  using TL = Tiles<V, PM, NT>;
+  A* scr;  // [RCH][NS] scratch for block reductions (inside the staging buffers)
+  V* stg;  // staging buffers
+  unsigned tseq;  // tiles consumed so far (the same in every streaming thread)
   int64_t rb, re;
   int nblocks;
   int buf;
@@ -141,8 +268,8 @@ struct Engine {
   int lane, warp;
   unsigned long long t_mark;
 
-  __device__ Engine(const SolveArgs<V>& args, Shared<PM>& s, A* scratch)
-      : a(args), sh(s), scr(scratch), buf(0), p(args.p), t_mark(0) {
+  __device__ Engine(const SolveArgs<V>& args, Shared<PM>& s, V* scratch)
+      : a(args), sh(s), scr(reinterpret_cast<A*>(scratch)), stg(scratch), tseq(0), buf(0), p(args.p), t_mark(0) {
     nblocks = gridDim.x;
     int64_t chunk = (a.n + nblocks - 1) / nblocks;
     chunk = (chunk + 31) / 32 * 32;
@@ -156,6 +283,84 @@ struct Engine {
 
   // first row of this streaming thread (rows advance by NS); control-warp threads get re
   __device__ __forceinline__ int64_t row0() const { return warp == 0 ? re : rb + (threadIdx.x - 32); }
+
+  __device__ __forceinline__ V* stage(int s) const { return stg + (size_t)s * (TL::STG / sizeof(V)); }
+  __device__ __forceinline__ static unsigned vbytes(int rows) {  // one vector's tile, whole 16 bytes
+    return (unsigned)(((size_t)rows * sizeof(V) + 15) / 16 * 16);
+  }
+
+  // (warp 1) entry c of the copy list: vector src into slot `slot` of a tile of T rows
+  __device__ __forceinline__ void cp_put(int c, const V* src, int slot, int T) {
+    sh.cp_src[c] = reinterpret_cast<const char*>(src);
+    sh.cp_dst[c] = (unsigned)((size_t)slot * T * sizeof(V));
+  }
+  // (warp 1) one tile of every listed vector into buffer sb, plus `extra` bytes that the caller
+  // copies itself after this returns; lane 0 announces the bytes before any copy is issued
+  __device__ __forceinline__ void cp_issue(int sb, int64_t r0, int rows, unsigned extra) {
+    const unsigned by = vbytes(rows);
+    unsigned long long* bar = &sh.tbar[sb];
+    char* d = reinterpret_cast<char*>(stage(sb));
+    const int n = sh.cp_n;
+    if (lane == 0) mbar_arrive_expect_tx(bar, (unsigned)n * by + extra);
+    __syncwarp();
+    const size_t off = (size_t)r0 * sizeof(V);
+    for (int c = lane; c < n; c += 32) bulk_g2s(d + sh.cp_dst[c], sh.cp_src[c] + off, by, bar);
+  }
+
+  // Staged streaming loop of the streaming warps over rows [rb, re) in tiles of T rows.  Tile i
+  // goes to buffer (tseq + i) mod NSTAGE: warp 1 issues its bulk copies with issue(buffer, r0,
+  // rows) (one mbarrier arrival announcing the bytes, then the copies), NSTAGE tiles ahead; every streaming
+  // thread waits for the buffer's phase (bounded), runs body(IC<G>, tile, o, r0 + o, rows) on
+  // groups of G rows (a partial last group row by row), and the streaming warps meet on named
+  // barrier 1 before the buffer is refilled.  The writes of the pass are fenced against the bulk
+  // (async-proxy) reads of later passes.  Returns false, with ctl->err set, if a wait ran out.
+  template <int T, int G, typename ISSUE, typename BODY>
+  __device__ __forceinline__ bool tiles(ISSUE&& issue, BODY&& body) {
+    static_assert(T >= 32 && T % G == 0 && T % 32 == 0, "tile shape");
+    const int st = threadIdx.x - 32;
+    const int64_t nrows = re - rb;
+    const int nt = nrows > 0 ? (int)((nrows + T - 1) / T) : 0;
+    if (warp == 1) {
+      fence_proxy_async();
+      for (int i = 0; i < TL::NSTAGE && i < nt; ++i)
+        issue((int)((tseq + i) % TL::NSTAGE), rb + (int64_t)i * T, (int)min((int64_t)T, nrows - (int64_t)i * T));
+    }
+    int i = 0;
+    for (; i < nt; ++i) {
+      const unsigned seq = tseq + i;
+      const int s = (int)(seq % TL::NSTAGE);
+      const int64_t r0 = rb + (int64_t)i * T;
+      const int rows = (int)min((int64_t)T, nrows - (int64_t)i * T);
+      if (mbar_wait(&sh.tbar[s], (seq / TL::NSTAGE) & 1u, a.barrier_limit_ns)) {
+        const V* tl = stage(s);
+#pragma unroll 1
+        for (int o = st * G; o < rows; o += NS * G) {
+          if (o + G <= rows) {
+            body(IC<G>{}, tl, o, r0 + o, rows);
+          } else {
+            for (int e = o; e < rows; ++e) body(IC<1>{}, tl, e, r0 + e, rows);
+          }
+        }
+      } else {
+        sh.terr = 1;
+      }
+      named_sync(1, NS);
+      if (*reinterpret_cast<volatile int*>(&sh.terr)) break;
+      if (warp == 1 && i + TL::NSTAGE < nt)
+        issue(s, r0 + (int64_t)TL::NSTAGE * T, (int)min((int64_t)T, nrows - (int64_t)(i + TL::NSTAGE) * T));
+    }
+    fence_proxy_async();
+    if (i < nt) {  // a wait ran out: record it, let the copies in flight land (bounded), give up
+      if (st == 0) {
+        atomicExch(&a.ctl->err, ST_ERR_TIMEOUT);
+        for (int k = i; k < nt && k < i + TL::NSTAGE; ++k)
+          mbar_wait(&sh.tbar[(tseq + k) % TL::NSTAGE], ((tseq + k) / TL::NSTAGE) & 1u, a.barrier_limit_ns);
+      }
+      return false;
+    }
+    tseq += nt;
+    return true;
+  }
 
   __device__ __forceinline__ int ring2p(int i) const { return ((i % (2 * p)) + 2 * p) % (2 * p); }
   __device__ __forceinline__ V* uslot(int i) const { return a.U + (int64_t)ring2p(i) * a.ld; }
@@ -188,6 +393,7 @@ struct Engine {
   template <int NVC>
   __device__ bool reduce(const A (&acc)[NVC], int nv) {
     const int tid = threadIdx.x;
+    fence_proxy_async();  // this pass's vector writes before later bulk (async-proxy) reads of them
 #pragma unroll
     for (int c0 = 0; c0 < NVC; c0 += RCH) {
       if (c0 < nv) {
@@ -348,68 +554,375 @@ struct Engine {
   // W_k = A u_{j0+k}; w'_{j0} = W_0 - sum_{i<j0} h_{j0,i} u_i (into W slot 0); inner products
   // u_{j0+k} . w'_{j0}; removed-vector products; ||W_0||^2.  The control warp runs the QR step of
   // iteration qr_j (if > 0) meanwhile.
+  // Staged per tile: u_{j0} .. u_{j0+p-1} (own rows; they also serve the gathers that fall in the
+  // tile), u_{j0-p} .. u_{j0-1}, and the tile's CSR segment: rowptr, colidx and values, copied in
+  // whole 16-byte units inside the arrays (entries outside the copied ranges are read directly).
+
+  // rowptr at this block's block-product tile boundaries (the CSR structure is fixed per solve)
+  __device__ void tabulate_csr_tiles() {
+    constexpr int T = TL::sp_rows();
+    const int64_t nrows = re - rb;
+    const int nt = nrows > 0 ? (int)((nrows + T - 1) / T) : 0;
+    const bool fit = nt <= TQMAX;
+    if (fit)
+      for (int i = threadIdx.x; i <= nt; i += NT) sh.tq[i] = __ldg(a.rowptr + min(rb + (int64_t)i * T, re));
+    if (threadIdx.x == 0) {
+      sh.tq_n = fit ? nt : -1;
+      sh.csr_nnz = __ldg(a.rowptr + a.n);
+    }
+    __syncthreads();
+  }
+
+  struct CsrTile {
+    bool ok;     // CSR segment staged
+    int nrp;     // rowptr entries staged (from r0)
+    int64_t qa;  // colidx / values staged for nonzeros [qa, qb)
+    int64_t qb;
+  };
+  // what is staged of the CSR arrays for block-product tile i (rows [r0, r0 + rows))
+  __device__ __forceinline__ CsrTile csr_tile(int i, int64_t r0, int rows, bool csr_al) const {
+    constexpr int T = TL::sp_rows();
+    CsrTile c{false, 0, 0, 0};
+    if (!csr_al || sh.tq_n < 0) return c;
+    const int64_t end4 = (a.n + 1) / 4 * 4;  // rowptr entries readable in whole 16-byte units
+    c.nrp = (int)max((int64_t)0, min((int64_t)((rows + 3) / 4 * 4), end4 - r0));
+    const int64_t nnz = sh.csr_nnz;
+    c.qa = (int64_t)sh.tq[i] / 4 * 4;
+    c.qb = min(((int64_t)sh.tq[i + 1] + 3) / 4 * 4, nnz / 4 * 4);
+    if (c.qb < c.qa) c.qb = c.qa;
+    c.ok = (c.qb - c.qa) <= (int64_t)8 * T;
+    return c;
+  }
+
   __device__ bool pass_spmm(int j0, int qr_j, int qr_l) {
-    A acc[LY::SP_N];
-#pragma unroll
-    for (int k = 0; k < LY::SP_N; ++k) acc[k] = 0;
+    A acc[LY::SP_N];  // written after the streaming loop
     int ng = 0;
 #pragma unroll
     for (int g = 0; g < NBMAX; ++g)
       if (g < sh.n_ghost) ng = g + 1;
     if (warp == 0) {
       if (qr_j > 0) qr_warp(qr_j, qr_l);
+#pragma unroll
+      for (int k = 0; k < LY::SP_N; ++k) acc[k] = 0;
     } else {
+      constexpr int T = TL::sp_rows(), G = TL::sp_group();
+      constexpr size_t OUK = (size_t)PM * T * sizeof(V), ORP = 2 * OUK;
+      constexpr size_t OCI = ORP + ((size_t)(T + 4) * 4 + 15) / 16 * 16;
+      constexpr size_t OCV = OCI + ((size_t)8 * T * 4 + 15) / 16 * 16;
+      static_assert(OCV + (size_t)8 * T * sizeof(V) <= TL::STG, "block-product tile");
+      const bool csr_al = ((reinterpret_cast<uintptr_t>(a.rowptr) | reinterpret_cast<uintptr_t>(a.colidx) |
+                            reinterpret_cast<uintptr_t>(a.vals)) & 15u) == 0;
       A cA[PM], sg[PM];
       const V* usrc[PM];
-      const V* uknown[PM];
 #pragma unroll
       for (int k = 0; k < PM; ++k) {
         cA[k] = (k < p) ? (A)sh.coefA[k] : (A)0;
         sg[k] = (k < p) ? (A)sig(j0 + k) : (A)0;
         usrc[k] = uslot(j0 + k);
-        uknown[k] = uslot(j0 - p + k);
       }
       const bool has_known = (j0 > 1);
       bool gact[NBMAX];
 #pragma unroll
       for (int g = 0; g < NBMAX; ++g) gact[g] = ghost_active(g, j0);
-      for (int64_t r = row0(); r < re; r += NS) {
-        A wk[PM];
+      A an = 0, adot[PM], agh[NBMAX];
 #pragma unroll
-        for (int k = 0; k < PM; ++k) wk[k] = 0;
-        const int32_t k0 = __ldg(a.rowptr + r), k1 = __ldg(a.rowptr + r + 1);
-        for (int32_t q = k0; q < k1; ++q) {
-          const int32_t c = __ldg(a.colidx + q);
-          const A v = __ldg(a.vals + q);
+      for (int k = 0; k < PM; ++k) adot[k] = 0;
 #pragma unroll
-          for (int k = 0; k < PM; ++k)
-            if (k < p) wk[k] += v * (A)usrc[k][c];
+      for (int g = 0; g < NBMAX; ++g) agh[g] = 0;
+      if (warp == 1) {  // copy list: u_{j0+k} into slot k, u_{j0-p+k} into slot PM + k
+        const int n = has_known ? 2 * p : p;
+        for (int c = lane; c < n; c += 32)
+          cp_put(c, c < p ? uslot(j0 + c) : uslot(j0 - p + (c - p)), c < p ? c : PM + (c - p), T);
+        if (lane == 0) sh.cp_n = n;
+        __syncwarp();
+      }
+      auto issue = [&](int sb, int64_t r0, int rows) __attribute__((always_inline)) {
+        const CsrTile c = csr_tile((int)((r0 - rb) / T), r0, rows, csr_al);
+        const unsigned bq = c.ok ? (unsigned)(c.qb - c.qa) : 0u;
+        const unsigned brp = c.ok ? (unsigned)c.nrp * 4u : 0u;
+        cp_issue(sb, r0, rows, brp + bq * (4u + (unsigned)sizeof(V)));
+        unsigned long long* bar = &sh.tbar[sb];
+        char* d = reinterpret_cast<char*>(stage(sb));
+        if (lane == 0 && brp) bulk_g2s(d + ORP, a.rowptr + r0, brp, bar);
+        if (lane == 1 && bq) bulk_g2s(d + OCI, a.colidx + c.qa, bq * 4u, bar);
+        if (lane == 2 && bq) bulk_g2s(d + OCV, a.vals + c.qa, bq * (unsigned)sizeof(V), bar);
+      };
+      auto body = [&](auto gt, const V* tl, int o, int64_t r, int rows) __attribute__((always_inline)) {
+        constexpr int GG = decltype(gt)::value;
+        constexpr int QC = 8;  // nonzeros of every row of the group fetched together
+        const int64_t r0 = r - o;  // first row of the tile
+        const CsrTile c = csr_tile((int)((r0 - rb) / T), r0, rows, csr_al);
+        const char* tb = reinterpret_cast<const char*>(tl);
+        const int32_t* rps = reinterpret_cast<const int32_t*>(tb + ORP);
+        const int32_t* cis = reinterpret_cast<const int32_t*>(tb + OCI);
+        const V* cvs = reinterpret_cast<const V*>(tb + OCV);
+        int32_t kb[GG + 1];
+#pragma unroll
+        for (int e = 0; e <= GG; ++e) {
+          const int lr = o + e;
+          kb[e] = (c.ok && lr < c.nrp) ? rps[lr] : __ldg(a.rowptr + r + e);
         }
+        A wk[PM][GG];
 #pragma unroll
-        for (int k = 0; k < PM; ++k) wk[k] *= sg[k];
-        A wp = wk[0];
+        for (int k = 0; k < PM; ++k)
+#pragma unroll
+          for (int e = 0; e < GG; ++e) wk[k][e] = 0;
+        int32_t mx = 0;
+#pragma unroll
+        for (int e = 0; e < GG; ++e) mx = max(mx, kb[e + 1] - kb[e]);
+        for (int32_t q0 = 0; q0 < mx; q0 += QC) {
+          int32_t ci[GG][QC];
+          A cv[GG][QC];
+#pragma unroll
+          for (int e = 0; e < GG; ++e)
+#pragma unroll
+            for (int qq = 0; qq < QC; ++qq) {
+              const int64_t q = (int64_t)kb[e] + q0 + qq;
+              ci[e][qq] = -1;
+              cv[e][qq] = 0;
+              if (q < kb[e + 1]) {
+                if (c.ok && q < c.qb) {
+                  ci[e][qq] = cis[q - c.qa];
+                  cv[e][qq] = cvs[q - c.qa];
+                } else {
+                  ci[e][qq] = __ldg(a.colidx + q);
+                  cv[e][qq] = (A)__ldg(a.vals + q);
+                }
+              }
+            }
+#pragma unroll
+          for (int e = 0; e < GG; ++e)
+#pragma unroll
+            for (int qq = 0; qq < QC; ++qq)
+              if (ci[e][qq] >= 0) {
+                const int64_t col = ci[e][qq];
+                const uint64_t ct = (uint64_t)(col - r0);
+                if (ct < (uint64_t)rows) {  // the column's row is staged
+#pragma unroll
+                  for (int k = 0; k < PM; ++k)
+                    if (k < p) wk[k][e] += cv[e][qq] * tl[k * T + ct];
+                } else {
+#pragma unroll
+                  for (int k = 0; k < PM; ++k)
+                    if (k < p) wk[k][e] += cv[e][qq] * (A)usrc[k][col];
+                }
+              }
+        }
+        A wp[GG], x[GG];
+#pragma unroll
+        for (int k = 0; k < PM; ++k)
+#pragma unroll
+          for (int e = 0; e < GG; ++e) wk[k][e] *= sg[k];
+#pragma unroll
+        for (int e = 0; e < GG; ++e) wp[e] = wk[0][e];
+        const V* sp = tl + o;
         if (has_known) {
 #pragma unroll
           for (int k = 0; k < PM; ++k)
-            if (k < p) wp -= cA[k] * (A)uknown[k][r];
-        }
-        wslot(0)[r] = (V)wp;
+            if (k < p) {
+              sld<GG>(sp + (PM + k) * T, x);
 #pragma unroll
-        for (int k = 1; k < PM; ++k)
-          if (k < p) wslot(k)[r] = (V)wk[k];
+              for (int e = 0; e < GG; ++e) wp[e] -= cA[k] * x[e];
+            }
+        }
 #pragma unroll
         for (int k = 0; k < PM; ++k)
-          if (k < p) acc[LY::SP_DOT + k] += (A)usrc[k][r] * wp;
+          if (k < p) {
+            sld<GG>(sp + k * T, x);
+#pragma unroll
+            for (int e = 0; e < GG; ++e) adot[k] += x[e] * wp[e];
+          }
 #pragma unroll
         for (int g = 0; g < NBMAX; ++g)
-          if (gact[g]) acc[LY::SP_GH + g] += (A)ghostv(g)[r] * wp;
-        acc[LY::SP_NRM] += wk[0] * wk[0];
-      }
+          if (gact[g]) {
+            vld<GG>(ghostv(g) + r, x);
+#pragma unroll
+            for (int e = 0; e < GG; ++e) agh[g] += x[e] * wp[e];
+          }
+#pragma unroll
+        for (int e = 0; e < GG; ++e) an += wk[0][e] * wk[0][e];
+        vst<GG>(wslot(0) + r, wp);
+#pragma unroll
+        for (int k = 1; k < PM; ++k)
+          if (k < p) vst<GG>(wslot(k) + r, wk[k]);
+      };
+      tiles<T, G>(issue, body);
+#pragma unroll
+      for (int k = 0; k < LY::SP_N; ++k) acc[k] = 0;
+      acc[LY::SP_NRM] = an;
+#pragma unroll
+      for (int k = 0; k < PM; ++k) acc[LY::SP_DOT + k] = adot[k];
+#pragma unroll
+      for (int g = 0; g < NBMAX; ++g) acc[LY::SP_GH + g] = agh[g];
     }
-    tick(a.ctl->t_stream);
-    if (!reduce(acc, ng > 0 ? LY::SP_GH + ng : LY::SP_GH)) return false;
+    tick(a.ctl->t_sp);
+    if (!reduce(acc, ng > 0 ? LY::SP_GH + ng : LY::SP_GH) || sh.terr) return false;
     tick(a.ctl->t_reduce);
     return true;
+  }
+
+  // Streaming part of the fused pass (all warps but the control warp).  EXTRA = false is the
+  // common case, compiled without removed-vector terms and with every bench vector staged.
+  // Staged slots: w'_j, u_j .. u_{j+p-1}, W_{t+1}, u_{j+1-p} .. u_{j-1}, bench vectors.
+  template <bool EXTRA>
+  __device__ __forceinline__ bool ba_stream(int j, int t, bool hasA, A (&acc)[LY::BA_N]) {
+    constexpr int NSL = 1 + 2 * PM + NBPRE;
+    constexpr int T = TL::rows(NSL), G = TL::group(NSL);
+    constexpr int SW = 0, SUB = 1, SW1 = 1 + PM, SUA = 2 + PM, SBN = 1 + 2 * PM;
+    constexpr int NBA = EXTRA ? NBMAX : NBPRE;  // bench accumulators
+    const int nb = a.nbench;
+    const int b0 = sh.bench_next;
+    const int nbp = min(nb - b0, NBPRE);  // bench vectors staged
+    const int ka = max(0, p - j);         // u_{j+1-p+k} exists for k >= ka
+    A cB[PM], cA[PM], cgb[NBMAX];
+#pragma unroll
+    for (int k = 0; k < PM; ++k) {
+      cB[k] = (k < p) ? (A)sh.coefB[k] : (A)0;
+      cA[k] = (k < p - 1) ? (A)sh.coefA[k] : (A)0;
+    }
+    const A cA_last = (A)sh.coefA[p - 1];  // multiplies u_j
+    bool gB[NBMAX], gA[NBMAX];
+#pragma unroll
+    for (int g = 0; g < NBMAX; ++g) {
+      gB[g] = EXTRA && ghost_active(g, j);
+      gA[g] = EXTRA && ghost_active(g, j + 1);
+      cgb[g] = gB[g] ? (A)sh.cgB[g] : (A)0;
+    }
+    V* wout = uslot(j + p);
+    const V* wcur = wslot(t);
+    V* wnext = wslot(t + 1 < p ? t + 1 : t);
+    A an = 0, aw1 = 0, adot[PM], agr[PM], accb[NBA], agh[EXTRA ? NBMAX : 1];
+#pragma unroll
+    for (int k = 0; k < PM; ++k) adot[k] = agr[k] = 0;
+#pragma unroll
+    for (int b = 0; b < NBA; ++b) accb[b] = 0;
+#pragma unroll
+    for (int g = 0; g < (EXTRA ? NBMAX : 1); ++g) agh[g] = 0;
+    if (warp == 1) {  // copy list: w'_j, u_j .. u_{j+p-1}, bench, then (A step) W_{t+1}, u_{j+1-p+k}
+      const int n = 1 + p + nbp + (hasA ? p - ka : 0);
+      for (int c = lane; c < n; c += 32) {
+        if (c == 0) {
+          cp_put(c, wcur, SW, T);
+        } else if (c <= p) {
+          cp_put(c, uslot(j + c - 1), SUB + c - 1, T);
+        } else if (c <= p + nbp) {
+          cp_put(c, bench(b0 + c - p - 1), SBN + c - p - 1, T);
+        } else if (c == p + nbp + 1) {
+          cp_put(c, wnext, SW1, T);
+        } else {
+          const int k = ka + c - (p + nbp + 2);
+          cp_put(c, uslot(j + 1 - p + k), SUA + k, T);
+        }
+      }
+      if (lane == 0) sh.cp_n = n;
+      __syncwarp();
+    }
+    auto issue = [&](int sb, int64_t r0, int rows) __attribute__((always_inline)) { cp_issue(sb, r0, rows, 0u); };
+    auto body = [&](auto gt, const V* tl, int o, int64_t r, int) __attribute__((always_inline)) {
+      constexpr int GG = decltype(gt)::value;
+      const V* sp = tl + o;
+      // the window slots are re-read from shared memory where they are needed (few live registers)
+      A w[GG], x[GG];
+      sld<GG>(sp + SW * T, w);
+      // B step of j
+#pragma unroll
+      for (int k = 0; k < PM; ++k)
+        if (k < p) {
+          sld<GG>(sp + (SUB + k) * T, x);
+#pragma unroll
+          for (int e = 0; e < GG; ++e) w[e] -= cB[k] * x[e];
+        }
+      if constexpr (EXTRA) {
+#pragma unroll
+        for (int g = 0; g < NBMAX; ++g)
+          if (gB[g]) {
+            vld<GG>(ghostv(g) + r, x);
+#pragma unroll
+            for (int e = 0; e < GG; ++e) w[e] -= cgb[g] * x[e];
+          }
+      }
+      vst<GG>(wout + r, w);
+#pragma unroll
+      for (int e = 0; e < GG; ++e) an += w[e] * w[e];
+#pragma unroll
+      for (int k = 1; k < PM; ++k)
+        if (k < p) {
+          sld<GG>(sp + (SUB + k) * T, x);
+#pragma unroll
+          for (int e = 0; e < GG; ++e) agr[k - 1] += w[e] * x[e];
+        }
+#pragma unroll
+      for (int b = 0; b < NBPRE; ++b)
+        if (b < nbp) {
+          sld<GG>(sp + (SBN + b) * T, x);
+#pragma unroll
+          for (int e = 0; e < GG; ++e) accb[b] += x[e] * w[e];
+        }
+      if constexpr (EXTRA) {
+#pragma unroll
+        for (int b = NBPRE; b < NBMAX; ++b)
+          if (b0 + b < nb) {
+            vld<GG>(bench(b0 + b) + r, x);
+#pragma unroll
+            for (int e = 0; e < GG; ++e) accb[b] += x[e] * w[e];
+          }
+      }
+      // A step of j+1
+      if (hasA) {
+        A w1[GG];
+        sld<GG>(sp + SW1 * T, w1);
+#pragma unroll
+        for (int e = 0; e < GG; ++e) aw1 += w1[e] * w1[e];
+#pragma unroll
+        for (int k = 0; k < PM - 1; ++k)
+          if (k < p - 1 && k >= ka) {
+            sld<GG>(sp + (SUA + k) * T, x);
+#pragma unroll
+            for (int e = 0; e < GG; ++e) w1[e] -= cA[k] * x[e];
+          }
+        sld<GG>(sp + SUB * T, x);
+#pragma unroll
+        for (int e = 0; e < GG; ++e) w1[e] -= cA_last * x[e];
+#pragma unroll
+        for (int k = 0; k < PM - 1; ++k)
+          if (k < p - 1) {
+            sld<GG>(sp + (SUB + k + 1) * T, x);
+#pragma unroll
+            for (int e = 0; e < GG; ++e) adot[k] += x[e] * w1[e];
+          }
+#pragma unroll
+        for (int e = 0; e < GG; ++e) adot[PM - 1] += w[e] * w1[e];
+        if constexpr (EXTRA) {
+#pragma unroll
+          for (int g = 0; g < NBMAX; ++g)
+            if (gA[g]) {
+              vld<GG>(ghostv(g) + r, x);
+#pragma unroll
+              for (int e = 0; e < GG; ++e) agh[g] += x[e] * w1[e];
+            }
+        }
+        vst<GG>(wnext + r, w1);
+      }
+    };
+    const bool ok = tiles<T, G>(issue, body);
+#pragma unroll
+    for (int k = 0; k < LY::BA_N; ++k) acc[k] = 0;
+    if constexpr (EXTRA) {
+#pragma unroll
+      for (int g = 0; g < NBMAX; ++g) acc[LY::BA_GH + g] = agh[g];
+    }
+    acc[LY::BA_NRM] = an;
+    acc[LY::BA_W1] = aw1;
+#pragma unroll
+    for (int k = 0; k < PM; ++k) acc[LY::BA_DOT + k] = adot[k];
+#pragma unroll
+    for (int k = 0; k < LY::GR; ++k) acc[LY::BA_GR + k] = agr[k];
+#pragma unroll
+    for (int v = 0; v < NBMAX; ++v)  // static register indices: acc[BA_BEN + b0 + b] = accb[b]
+#pragma unroll
+      for (int b = 0; b < NBA; ++b)
+        if (b0 + b == v) acc[LY::BA_BEN + v] = accb[b];
+    return ok;
   }
 
   // ---- fused pass of iteration j: B step of j (+ A step of j+1 when hasA) ---------------------
@@ -419,9 +932,7 @@ struct Engine {
   //     vectors active at j+1.  Also ||w_j||^2, ||W_{t+1}||^2, w_j . u_{j+k} (Gram entries) and
   //     bench . w_j.  The control warp runs the QR step of iteration qr_j (if > 0) meanwhile.
   __device__ bool pass_ba(int j, int t, bool hasA, int qr_j, int qr_l) {
-    A acc[LY::BA_N];
-#pragma unroll
-    for (int k = 0; k < LY::BA_N; ++k) acc[k] = 0;
+    A acc[LY::BA_N];  // written after the streaming loop (not live across it)
     int ng = 0;
 #pragma unroll
     for (int g = 0; g < NBMAX; ++g)
@@ -429,77 +940,16 @@ struct Engine {
     const int nb = a.nbench;
     if (warp == 0) {
       if (qr_j > 0) qr_warp(qr_j, qr_l);
+#pragma unroll
+      for (int k = 0; k < LY::BA_N; ++k) acc[k] = 0;
+    } else if (ng > 0 || nb - sh.bench_next > NBPRE) {
+      ba_stream<true>(j, t, hasA, acc);  // removed vectors active, or many bench vectors
     } else {
-      A cB[PM], cA[PM], cgb[NBMAX];
-      const V* ub[PM];
-      const V* ua[PM];
-#pragma unroll
-      for (int k = 0; k < PM; ++k) {
-        cB[k] = (k < p) ? (A)sh.coefB[k] : (A)0;
-        cA[k] = (k < p - 1) ? (A)sh.coefA[k] : (A)0;
-        ub[k] = uslot(j + k);
-        ua[k] = uslot(j + 1 - p + k);
-      }
-      const A cA_last = (A)sh.coefA[p - 1];  // multiplies u_j, loaded as ub[0]
-      bool gB[NBMAX], gA[NBMAX];
-#pragma unroll
-      for (int g = 0; g < NBMAX; ++g) {
-        gB[g] = ghost_active(g, j);
-        gA[g] = ghost_active(g, j + 1);
-        cgb[g] = gB[g] ? (A)sh.cgB[g] : (A)0;
-      }
-      const bool known_ok = (j + 1 - p >= 1);  // every u_i with i = j+1-p+k, k < p-1, exists
-      const int b0 = sh.bench_next;
-      V* wout = uslot(j + p);
-      const V* wcur = wslot(t);
-      V* wnext = wslot(t + 1 < p ? t + 1 : t);
-      for (int64_t r = row0(); r < re; r += NS) {
-        A w = wcur[r];
-        A ubv[PM];
-#pragma unroll
-        for (int k = 0; k < PM; ++k)
-          if (k < p) {
-            ubv[k] = ub[k][r];
-            w -= cB[k] * ubv[k];
-          }
-#pragma unroll
-        for (int g = 0; g < NBMAX; ++g)
-          if (gB[g]) w -= cgb[g] * (A)ghostv(g)[r];
-        wout[r] = (V)w;
-        acc[LY::BA_NRM] += w * w;
-#pragma unroll
-        for (int k = 1; k < PM; ++k)
-          if (k < p) acc[LY::BA_GR + k - 1] += w * ubv[k];
-#pragma unroll
-        for (int b = 0; b < NBMAX; ++b)
-          if (b >= b0 && b < nb) acc[LY::BA_BEN + b] += (A)bench(b)[r] * w;
-        if (hasA) {
-          A w1 = wnext[r];
-          acc[LY::BA_W1] += w1 * w1;
-          if (known_ok) {
-#pragma unroll
-            for (int k = 0; k < PM - 1; ++k)
-              if (k < p - 1) w1 -= cA[k] * (A)ua[k][r];
-          } else {
-#pragma unroll
-            for (int k = 0; k < PM - 1; ++k)
-              if (k < p - 1 && j + 1 - p + k >= 1) w1 -= cA[k] * (A)ua[k][r];
-          }
-          w1 -= cA_last * ubv[0];
-          wnext[r] = (V)w1;
-#pragma unroll
-          for (int k = 0; k < PM - 1; ++k)
-            if (k < p - 1) acc[LY::BA_DOT + k] += ubv[k + 1] * w1;
-          acc[LY::BA_DOT + PM - 1] += w * w1;
-#pragma unroll
-          for (int g = 0; g < NBMAX; ++g)
-            if (gA[g]) acc[LY::BA_GH + g] += (A)ghostv(g)[r] * w1;
-        }
-      }
+      ba_stream<false>(j, t, hasA, acc);
     }
     tick(a.ctl->t_stream);
     const int nv = ng > 0 ? LY::BA_GH + ng : LY::BA_BEN + nb;
-    if (!reduce(acc, nv)) return false;
+    if (!reduce(acc, nv) || sh.terr) return false;  // (sh.terr is read after the reduction's block barrier)
     for (int v = threadIdx.x; v < NVMAX; v += NT) sh.rba[v] = (v < nv) ? sh.red[v] : 0.0;
     __syncthreads();
     tick(a.ctl->t_reduce);
@@ -692,61 +1142,147 @@ struct Engine {
     if constexpr (sizeof(A) == 4) return sh.bcf[b][par][l]; else return sh.bc[b][par][l];
   }
 
-  __device__ void pass_dir(int j0, int L, int cyc, bool update_bench) {
+  // Staged slots: m_{j0-2p} .. m_{j0-1}, u_{j0} .. u_{j0+p-1}, the iterate rows (p values per row,
+  // when p * sizeof(V) is a whole number of 16-byte units and X is 16-byte aligned), bench vectors.
+  __device__ bool pass_dir(int j0, int L, int cyc, bool update_bench) {
     if (warp > 0) {
+      constexpr int NSL = 4 * PM + NBPRE;
+      constexpr int T = TL::rows(NSL), G = TL::group(NSL);
+      constexpr int SMO = 0, SUV = 2 * PM, SX = 3 * PM, SBN = 4 * PM;
       const int nb = a.nbench, b0 = sh.bench_next;
-      const V* mold[2 * PM];
-      bool mvalid[2 * PM];
+      const int nbp = update_bench ? min(nb - b0, NBPRE) : 0;
+      const int q0 = max(2 * PM - 2 * p, 2 * PM + 1 - j0);  // first window position holding some m_i
+      V* mout[PM];  // m_{j0+l}
 #pragma unroll
-      for (int q = 0; q < 2 * PM; ++q) {
-        int i = j0 - 2 * PM + q;  // m_i held at window position q
-        mvalid[q] = (q >= 2 * PM - 2 * p) && i >= 1;
-        mold[q] = mslot(i);
+      for (int l = 0; l < PM; ++l) mout[l] = mslot(j0 + l);
+      const bool xst = ((p * (int)sizeof(V)) % 16 == 0) && ((reinterpret_cast<uintptr_t>(a.X) & 15u) == 0);
+      const bool xvec = xst && (p == PM);  // whole-vector iterate stores
+      if (warp == 1) {  // copy list: m_{j0-2PM+q} (q >= q0), u_{j0+l}, bench
+        const int nm = 2 * PM - q0, n = nm + p + nbp;
+        for (int c = lane; c < n; c += 32) {
+          if (c < nm)
+            cp_put(c, mslot(j0 - 2 * PM + q0 + c), SMO + q0 + c, T);
+          else if (c < nm + p)
+            cp_put(c, uslot(j0 + c - nm), SUV + c - nm, T);
+          else
+            cp_put(c, bench(b0 + c - nm - p), SBN + c - nm - p, T);
+        }
+        if (lane == 0) sh.cp_n = n;
+        __syncwarp();
       }
-      for (int64_t r = row0(); r < re; r += NS) {
-        A mw[3 * PM];
+      auto issue = [&](int sb, int64_t r0, int rows) __attribute__((always_inline)) {
+        const unsigned bx = xst ? (unsigned)((size_t)rows * p * sizeof(V)) : 0u;
+        cp_issue(sb, r0, rows, bx);
+        if (lane == 0 && bx) bulk_g2s(stage(sb) + SX * T, a.X + r0 * p, bx, &sh.tbar[sb]);
+      };
+      auto body = [&](auto gt, const V* tl, int o, int64_t r, int) __attribute__((always_inline)) {
+        constexpr int GG = decltype(gt)::value;
+        const V* sp = tl + o;
+        A mw[3 * PM][GG];
 #pragma unroll
-        for (int q = 0; q < 2 * PM; ++q) mw[q] = mvalid[q] ? (A)mold[q][r] : (A)0;
-        A uv[PM];
+        for (int q = 0; q < 2 * PM; ++q)
+          if (q >= q0) {
+            sld<GG>(sp + (SMO + q) * T, mw[q]);
+          } else {
 #pragma unroll
-        for (int l = 0; l < PM; ++l) uv[l] = (l < p) ? (A)uslot(j0 + l)[r] : (A)0;
+            for (int e = 0; e < GG; ++e) mw[q][e] = 0;
+          }
+        A uv[PM][GG];
+#pragma unroll
+        for (int l = 0; l < PM; ++l)
+          if (l < p) {
+            sld<GG>(sp + (SUV + l) * T, uv[l]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < GG; ++e) uv[l][e] = 0;
+          }
 #pragma unroll
         for (int l = 0; l < PM; ++l) {
           if (l < L) {
-            A m = cdirA(l) * uv[l];
+            const A ca = cdirA(l);
 #pragma unroll
-            for (int q = 0; q < 2 * PM; ++q) m += cdirB(l, q) * mw[l + q];
-            mw[2 * PM + l] = m;
-            mslot(j0 + l)[r] = (V)m;
+            for (int e = 0; e < GG; ++e) mw[2 * PM + l][e] = ca * uv[l][e];
+#pragma unroll
+            for (int q = 0; q < 2 * PM; ++q) {
+              const A cb = cdirB(l, q);
+#pragma unroll
+              for (int e = 0; e < GG; ++e) mw[2 * PM + l][e] += cb * mw[l + q][e];
+            }
+            vst<GG>(mout[l] + r, mw[2 * PM + l]);
           } else {
-            mw[2 * PM + l] = 0;
+#pragma unroll
+            for (int e = 0; e < GG; ++e) mw[2 * PM + l][e] = 0;
           }
         }
+        // iterate rows r .. r+GG-1 (row-major, p per row)
+        const V* xsrc = xst ? tl + SX * T + (size_t)o * p : a.X + r * p;
         V* xr = a.X + r * (int64_t)p;
+        A xs[GG][PM];
 #pragma unroll
-        for (int c = 0; c < PM; ++c)
-          if (c < p) {
-            A s = xr[c];
+        for (int e = 0; e < GG; ++e)
 #pragma unroll
-            for (int l = 0; l < PM; ++l)
-              if (l < L) s += mw[2 * PM + l] * cZ(l, c);
-            xr[c] = (V)s;
+          for (int c = 0; c < PM; ++c)
+            if (c < p) xs[e][c] = xsrc[e * p + c];
+#pragma unroll
+        for (int e = 0; e < GG; ++e)
+#pragma unroll
+          for (int c = 0; c < PM; ++c)
+            if (c < p) {
+              A s = xs[e][c];
+#pragma unroll
+              for (int l = 0; l < PM; ++l)
+                if (l < L) s += mw[2 * PM + l][e] * cZ(l, c);
+              xs[e][c] = s;
+            }
+        if (xvec) {  // p == PM: 16-byte stores, flat index f = e * PM + c
+          constexpr int W = 16 / sizeof(V);
+#pragma unroll
+          for (int f0 = 0; f0 < GG * PM; f0 += W) {
+            if constexpr (GG * PM % W == 0) {
+              V tmp[W];
+#pragma unroll
+              for (int i = 0; i < W; ++i) tmp[i] = xs[(f0 + i) / PM][(f0 + i) % PM];
+              vst<W>(xr + f0, tmp);
+            }
           }
+          if constexpr (GG * PM % W != 0) {
+#pragma unroll
+            for (int e = 0; e < GG; ++e)
+#pragma unroll
+              for (int c = 0; c < PM; ++c) xr[e * PM + c] = xs[e][c];
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < GG; ++e)
+#pragma unroll
+            for (int c = 0; c < PM; ++c)
+              if (c < p) xr[e * p + c] = xs[e][c];
+        }
         if (update_bench) {
 #pragma unroll
           for (int b = 0; b < NBMAX; ++b)
-            if (b >= b0 && b < nb) {
-              A v = bench(b)[r];
+            if (b0 + b < nb) {
+              A v[GG];
+              if (b < NBPRE)
+                sld<GG>(sp + (SBN + (b < NBPRE ? b : 0)) * T, v);
+              else
+                vld<GG>(bench(b0 + b) + r, v);
 #pragma unroll
               for (int l = 0; l < PM; ++l)
-                if (l < p) v -= cbc(b, cyc & 1, l) * uv[l];
-              bench(b)[r] = (V)v;
+                if (l < p) {
+                  const A cc = cbc(b0 + b, cyc & 1, l);
+#pragma unroll
+                  for (int e = 0; e < GG; ++e) v[e] -= cc * uv[l][e];
+                }
+              vst<GG>(bench(b0 + b) + r, v);
             }
         }
-      }
+      };
+      tiles<T, G>(issue, body);
     }
     __syncthreads();
-    tick(a.ctl->t_stream);
+    tick(a.ctl->t_dir);
+    return sh.terr == 0;  // uniform over the block
   }
 
   // ---- control warp: coefficients between passes --------------------------------------------
@@ -974,6 +1510,11 @@ struct Engine {
     t_mark = t_start;
     for (int i = tid; i < (int)(sizeof(Shared<PM>) / 8); i += NT) reinterpret_cast<double*>(&sh)[i] = 0.0;
     __syncthreads();
+    if (tid == 0) {
+      for (int k = 0; k < TL::NSTAGE; ++k) mbar_init(&sh.tbar[k], 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
     // the rotation window starts as the identity: P[i][i] = 1 for the columns j-p .. j+p-1 of j = 1
     for (int c = tid; c < 2 * p; c += NT) {
       int i = 1 - p + c;
@@ -1041,6 +1582,7 @@ struct Engine {
     }
     __syncthreads();
 
+    tabulate_csr_tiles();
     // ---- band iterations, one cycle of p iterations at a time ----
     int cycle = 1;
     bool qr_pending = false;  // QR step of the last iteration of the previous cycle not done yet
@@ -1066,7 +1608,7 @@ struct Engine {
         if (p > 1) ctl_coefA(j0 + 1);
       }
       __syncthreads();
-      if (cycle > 1) pass_dir(j0 - p, p, cycle - 1, true);  // directions of the previous cycle
+      if (cycle > 1 && !pass_dir(j0 - p, p, cycle - 1, true)) return fail(t_start);  // previous cycle
       tick(ctl->t_scalar);
       for (int t = 0; t < p; ++t) {
         const int jj = j0 + t;
@@ -1136,7 +1678,7 @@ struct Engine {
   // directions and iterate for the L completed iterations of cycle `cyc` starting at j0; stop:
   // 1 converged, 2 error, 3 iteration limit
   __device__ void end_cycle(unsigned long long t_start, int j0, int L, int cyc, int stop) {
-    if (L > 0) pass_dir(j0, L, cyc, false);
+    if (L > 0 && !pass_dir(j0, L, cyc, false)) return fail(t_start);
     finish(t_start, j0 + L - 1, stop);
   }
 
@@ -1168,15 +1710,17 @@ struct Engine {
 
 template <typename V, int PM, int NT>
 constexpr size_t solve_smem_bytes() {
-  return ((sizeof(Shared<PM>) + 15) / 16) * 16 + sizeof(V) * (size_t)16 * (NT - 32);
+  static_assert(Tiles<V, PM, NT>::STG * Tiles<V, PM, NT>::NSTAGE >= sizeof(V) * (size_t)16 * (NT - 32),
+                "reduction scratch");
+  return Tiles<V, PM, NT>::smem_bytes();
 }
 
 template <typename V, int PM, int NT>
 __global__ void __launch_bounds__(NT, 1) bminres_solve_kernel(SolveArgs<V> args) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   Shared<PM>& sh = *reinterpret_cast<Shared<PM>*>(smem_raw);
-  V* scr = reinterpret_cast<V*>(smem_raw + ((sizeof(Shared<PM>) + 15) / 16) * 16);
-  Engine<V, PM, NT> e(args, sh, scr);
+  V* stg = reinterpret_cast<V*>(smem_raw + Tiles<V, PM, NT>::SH);
+  Engine<V, PM, NT> e(args, sh, stg);
   e.run();
 }
 
