@@ -650,6 +650,7 @@ struct Engine {
       auto body = [&](auto gt, const V* tl, int o, int64_t r, int rows) __attribute__((always_inline)) {
         constexpr int GG = decltype(gt)::value;
         constexpr int QC = 8;  // nonzeros of every row of the group fetched together
+        constexpr int QH = (PM * sizeof(V) <= 32) ? QC : (PM * sizeof(V) <= 64 ? QC / 2 : 1);  // gathers in flight
         const int64_t r0 = r - o;  // first row of the tile
         const CsrTile c = csr_tile((int)((r0 - rb) / T), r0, rows, csr_al);
         const char* tb = reinterpret_cast<const char*>(tl);
@@ -690,23 +691,38 @@ struct Engine {
                 }
               }
             }
+          // columns whose rows lie in the tile come from the staged copy; the others are gathered
+          // from global memory by predicated loads, all issued before any is used (one round trip
+          // per row of the group)
 #pragma unroll
-          for (int e = 0; e < GG; ++e)
+          for (int e = 0; e < GG; ++e) {
+            bool out[QC];
 #pragma unroll
-            for (int qq = 0; qq < QC; ++qq)
-              if (ci[e][qq] >= 0) {
-                const int64_t col = ci[e][qq];
-                const uint64_t ct = (uint64_t)(col - r0);
-                if (ct < (uint64_t)rows) {  // the column's row is staged
+            for (int qq = 0; qq < QC; ++qq) {
+              const int64_t col = ci[e][qq];
+              const uint64_t ct = (uint64_t)(col - r0);
+              out[qq] = ci[e][qq] >= 0 && ct >= (uint64_t)rows;
+              if (ci[e][qq] >= 0 && ct < (uint64_t)rows) {
 #pragma unroll
-                  for (int k = 0; k < PM; ++k)
-                    if (k < p) wk[k][e] += cv[e][qq] * tl[k * T + ct];
-                } else {
-#pragma unroll
-                  for (int k = 0; k < PM; ++k)
-                    if (k < p) wk[k][e] += cv[e][qq] * (A)usrc[k][col];
-                }
+                for (int k = 0; k < PM; ++k)
+                  if (k < p) wk[k][e] += cv[e][qq] * tl[k * T + ct];
               }
+            }
+#pragma unroll
+            for (int h = 0; h < QC; h += QH) {
+              A gv[QH][PM];
+#pragma unroll
+              for (int qq = 0; qq < QH; ++qq)
+#pragma unroll
+                for (int k = 0; k < PM; ++k)
+                  gv[qq][k] = (out[h + qq] && k < p) ? (A)usrc[k][out[h + qq] ? ci[e][h + qq] : 0] : (A)0;
+#pragma unroll
+              for (int qq = 0; qq < QH; ++qq)
+#pragma unroll
+                for (int k = 0; k < PM; ++k)
+                  if (k < p) wk[k][e] += cv[e][h + qq] * gv[qq][k];
+            }
+          }
         }
         A wp[GG], x[GG];
 #pragma unroll
