@@ -20,8 +20,7 @@ enum : int {
 
 // Device-global control block, one per handle.  Zeroed before every persistent launch.
 struct Ctl {
-  unsigned bar_count;  // arrivals at the current barrier
-  unsigned bar_gen;    // barrier generation
+  unsigned long long bar_arrived;  // grid-barrier arrivals since the launch (nblocks per barrier)
   int err;             // set to ST_ERR_TIMEOUT by a block whose wait ran out
   int status;          // final status (block 0)
   int iters;           // band iterations
@@ -44,36 +43,37 @@ __device__ __forceinline__ unsigned long long gtimer() {
   return t;
 }
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 __device__ __forceinline__ int ld_volatile_int(const int* p) { return *(volatile const int*)p; }
 
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).  Every wait is bounded:
-// after `limit_ns` the waiting block records ST_ERR_TIMEOUT in ctl->err and returns false, so a
-// broken schedule ends the kernel instead of hanging the GPU.  Returns false if any block has
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).  Thread 0 of each block adds
+// one to a 64-bit arrival counter (release: the block's writes, ordered before it by the block
+// barrier, become visible with it) and waits (acquire) until the counter reaches nblocks * epoch,
+// `epoch` counting the barriers this block has passed (the same sequence in every block).  Every
+// wait is bounded: after `limit_ns` the block records ST_ERR_TIMEOUT in ctl->err and returns false,
+// so a broken schedule ends the kernel instead of hanging the GPU.  Returns false if any block has
 // recorded an error.
-__device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks, unsigned long long limit_ns) {
+__device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks, unsigned long long& epoch,
+                                             unsigned long long limit_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    unsigned gen = ld_acquire(&ctl->bar_gen);
-    __threadfence();
-    unsigned arrived = atomicAdd(&ctl->bar_count, 1u) + 1u;
-    if (arrived == nblocks) {
-      atomicExch(&ctl->bar_count, 0u);
-      __threadfence();
-      st_release(&ctl->bar_gen, gen + 1u);
-    } else {
-      unsigned long long t0 = gtimer();
+    epoch += 1;
+    const unsigned long long target = epoch * nblocks;
+    red_release_add64(&ctl->bar_arrived, 1ull);
+    if (ld_acquire64(&ctl->bar_arrived) < target) {
+      const unsigned long long t0 = gtimer();
       unsigned spins = 0;
-      while (ld_acquire(&ctl->bar_gen) == gen) {
+      while (ld_acquire64(&ctl->bar_arrived) < target) {
         if ((++spins & 63u) == 0u) {
           if (gtimer() - t0 > limit_ns) {
             atomicExch(&ctl->err, ST_ERR_TIMEOUT);
@@ -87,7 +87,6 @@ __device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks, unsigne
         }
       }
     }
-    __threadfence();
     if (ld_volatile_int(&ctl->err) != 0) ok = 0;
     s_ok = ok;
   }

@@ -36,6 +36,8 @@
 //   X     row-major n x p iterate (FP64 mode) or correction D (mixed mode, zeroed on entry)
 // U, M and Ghost must be zero on entry.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace bmr {
@@ -88,6 +90,7 @@ constexpr int TQMAX = 512;  // tiles per block whose CSR offsets are tabulated f
 template <int PM>
 struct __align__(16) Shared {
   unsigned long long tbar[NSTAGE_MAX];  // completion barriers of the staging buffers
+  unsigned long long bar_epoch;         // grid barriers this block has passed (thread 0)
   int tq[TQMAX + 1];                // rowptr at the block-product tile boundaries of this block
   int tq_n;                         // tiles tabulated (-1: too many, CSR read directly)
   int csr_nnz;                      // rowptr[n]
@@ -131,6 +134,7 @@ struct __align__(16) Shared {
   // single-precision copies of the direction-pass coefficients (used by FP32 vectors, so that the
   // row loop does no double -> float conversions, which run on the slow FP64 pipe)
   float dirAf[PM], dirBf[PM][2 * PM], Zcf[PM][PM], bcf[NBMAX][2][PM];
+  float coefAf[PM], coefBf[PM], cgBf[NBMAX];  // single-precision copies of coefA, coefB, cgB
   double red[Layout<PM>::NVMAX];   // values of the last grid reduction
   double rba[Layout<PM>::NVMAX];   // saved values of the last fused pass
   double s2[Layout<PM>::NVMAX][32];
@@ -204,6 +208,15 @@ __device__ __forceinline__ void sld(const double* p, double (&x)[G]) {
   }
 }
 
+// Per-thread accumulation of inner products (a += x * y), block-level sums (a += b) and the FP64
+// value of an accumulator, for every vector element type.
+__device__ __forceinline__ void dot_add(double& a, double x, double y) { a = fma(x, y, a); }
+__device__ __forceinline__ void dot_add(float& a, float x, float y) { a = fmaf(x, y, a); }
+__device__ __forceinline__ void dot_sum(double& a, double b) { a += b; }
+__device__ __forceinline__ void dot_sum(float& a, float b) { a += b; }
+__device__ __forceinline__ double dot_val(double a) { return a; }
+__device__ __forceinline__ double dot_val(float a) { return (double)a; }
+
 // Shared-memory staging of the streaming passes: NSTAGE buffers of STG bytes after the Shared block
 // (the reduction scratch reuses them).  A pass that streams `nsl` vector slots per row works on
 // tiles of rows(nsl) rows; its consumers take groups of group(nsl) consecutive rows.
@@ -249,7 +262,8 @@ struct Tiles {
 
 template <typename V, int PM, int NT>
 struct Engine {
-  using A = V;  // per-thread accumulation in the vector precision
+  using A = V;  // arithmetic on vector elements
+  using R = A;  // per-thread inner-product accumulators
   using LY = Layout<PM>;
   static constexpr int NVMAX = LY::NVMAX;
   static constexpr int NS = NT - 32;  // streaming threads (warps 1..NT/32-1)
@@ -390,9 +404,11 @@ struct Engine {
   // Inside the block: transpose the streaming threads' values through shared memory and sum in a
   // fixed order; across blocks: every block sums the per-block partials of all blocks in the same
   // fixed order.  Returns false if a grid barrier failed.
-  template <int NVC>
-  __device__ bool reduce(const A (&acc)[NVC], int nv) {
+  template <typename T, int NVC>
+  __device__ bool reduce(const T (&acc)[NVC], int nv) {
+    static_assert(sizeof(T) <= 8, "reduction scratch element");
     const int tid = threadIdx.x;
+    T* sc = reinterpret_cast<T*>(scr);
     fence_proxy_async();  // this pass's vector writes before later bulk (async-proxy) reads of them
 #pragma unroll
     for (int c0 = 0; c0 < NVC; c0 += RCH) {
@@ -400,16 +416,16 @@ struct Engine {
         if (warp > 0) {
 #pragma unroll
           for (int v = 0; v < RCH; ++v)
-            if (c0 + v < NVC && c0 + v < nv) scr[v * NS + tid - 32] = acc[c0 + v];
+            if (c0 + v < NVC && c0 + v < nv) sc[v * NS + tid - 32] = acc[c0 + v];
         }
         __syncthreads();
         const int cn = (nv - c0 < RCH) ? nv - c0 : RCH;
         for (int task = tid; task < cn * 32; task += NT) {
           int v = task >> 5, l = task & 31;
-          A s = scr[v * NS + l];
+          T s = sc[v * NS + l];
 #pragma unroll
-          for (int q = 1; q < NS / 32; ++q) s += scr[v * NS + l + 32 * q];
-          sh.s2[c0 + v][l] = (double)s;
+          for (int q = 1; q < NS / 32; ++q) dot_sum(s, sc[v * NS + l + 32 * q]);
+          sh.s2[c0 + v][l] = dot_val(s);
         }
         __syncthreads();
       }
@@ -424,7 +440,7 @@ struct Engine {
     for (int v = tid; v < nv; v += NT)
       part[(int64_t)v * nblocks + blockIdx.x] = (sh.d4[v][0] + sh.d4[v][1]) + (sh.d4[v][2] + sh.d4[v][3]);
     buf ^= 1;
-    if (!grid_barrier(a.ctl, nblocks, a.barrier_limit_ns)) return false;
+    if (!grid_barrier(a.ctl, nblocks, sh.bar_epoch, a.barrier_limit_ns)) return false;
     for (int task = tid; task < nv * 32; task += NT) {
       int v = task >> 5, l = task & 31;
       const double* pv = part + (int64_t)v * nblocks;
@@ -595,7 +611,7 @@ struct Engine {
   }
 
   __device__ bool pass_spmm(int j0, int qr_j, int qr_l) {
-    A acc[LY::SP_N];  // written after the streaming loop
+    R acc[LY::SP_N];  // written after the streaming loop
     int ng = 0;
 #pragma unroll
     for (int g = 0; g < NBMAX; ++g)
@@ -603,7 +619,7 @@ struct Engine {
     if (warp == 0) {
       if (qr_j > 0) qr_warp(qr_j, qr_l);
 #pragma unroll
-      for (int k = 0; k < LY::SP_N; ++k) acc[k] = 0;
+      for (int k = 0; k < LY::SP_N; ++k) acc[k] = R{};
     } else {
       constexpr int T = TL::sp_rows(), G = TL::sp_group();
       constexpr size_t OUK = (size_t)PM * T * sizeof(V), ORP = 2 * OUK;
@@ -616,7 +632,7 @@ struct Engine {
       const V* usrc[PM];
 #pragma unroll
       for (int k = 0; k < PM; ++k) {
-        cA[k] = (k < p) ? (A)sh.coefA[k] : (A)0;
+        cA[k] = (k < p) ? ccoefA(k) : (A)0;
         sg[k] = (k < p) ? (A)sig(j0 + k) : (A)0;
         usrc[k] = uslot(j0 + k);
       }
@@ -624,11 +640,11 @@ struct Engine {
       bool gact[NBMAX];
 #pragma unroll
       for (int g = 0; g < NBMAX; ++g) gact[g] = ghost_active(g, j0);
-      A an = 0, adot[PM], agh[NBMAX];
+      R an{}, adot[PM], agh[NBMAX];
 #pragma unroll
-      for (int k = 0; k < PM; ++k) adot[k] = 0;
+      for (int k = 0; k < PM; ++k) adot[k] = R{};
 #pragma unroll
-      for (int g = 0; g < NBMAX; ++g) agh[g] = 0;
+      for (int g = 0; g < NBMAX; ++g) agh[g] = R{};
       if (warp == 1) {  // copy list: u_{j0+k} into slot k, u_{j0-p+k} into slot PM + k
         const int n = has_known ? 2 * p : p;
         for (int c = lane; c < n; c += 32)
@@ -746,17 +762,17 @@ struct Engine {
           if (k < p) {
             sld<GG>(sp + k * T, x);
 #pragma unroll
-            for (int e = 0; e < GG; ++e) adot[k] += x[e] * wp[e];
+            for (int e = 0; e < GG; ++e) dot_add(adot[k], x[e], wp[e]);
           }
 #pragma unroll
         for (int g = 0; g < NBMAX; ++g)
           if (gact[g]) {
             vld<GG>(ghostv(g) + r, x);
 #pragma unroll
-            for (int e = 0; e < GG; ++e) agh[g] += x[e] * wp[e];
+            for (int e = 0; e < GG; ++e) dot_add(agh[g], x[e], wp[e]);
           }
 #pragma unroll
-        for (int e = 0; e < GG; ++e) an += wk[0][e] * wk[0][e];
+        for (int e = 0; e < GG; ++e) dot_add(an, wk[0][e], wk[0][e]);
         vst<GG>(wslot(0) + r, wp);
 #pragma unroll
         for (int k = 1; k < PM; ++k)
@@ -764,7 +780,7 @@ struct Engine {
       };
       tiles<T, G>(issue, body);
 #pragma unroll
-      for (int k = 0; k < LY::SP_N; ++k) acc[k] = 0;
+      for (int k = 0; k < LY::SP_N; ++k) acc[k] = R{};
       acc[LY::SP_NRM] = an;
 #pragma unroll
       for (int k = 0; k < PM; ++k) acc[LY::SP_DOT + k] = adot[k];
@@ -781,7 +797,7 @@ struct Engine {
   // common case, compiled without removed-vector terms and with every bench vector staged.
   // Staged slots: w'_j, u_j .. u_{j+p-1}, W_{t+1}, u_{j+1-p} .. u_{j-1}, bench vectors.
   template <bool EXTRA>
-  __device__ __forceinline__ bool ba_stream(int j, int t, bool hasA, A (&acc)[LY::BA_N]) {
+  __device__ __forceinline__ bool ba_stream(int j, int t, bool hasA, R (&acc)[LY::BA_N]) {
     constexpr int NSL = 1 + 2 * PM + NBPRE;
     constexpr int T = TL::rows(NSL), G = TL::group(NSL);
     constexpr int SW = 0, SUB = 1, SW1 = 1 + PM, SUA = 2 + PM, SBN = 1 + 2 * PM;
@@ -793,27 +809,27 @@ struct Engine {
     A cB[PM], cA[PM], cgb[NBMAX];
 #pragma unroll
     for (int k = 0; k < PM; ++k) {
-      cB[k] = (k < p) ? (A)sh.coefB[k] : (A)0;
-      cA[k] = (k < p - 1) ? (A)sh.coefA[k] : (A)0;
+      cB[k] = (k < p) ? ccoefB(k) : (A)0;
+      cA[k] = (k < p - 1) ? ccoefA(k) : (A)0;
     }
-    const A cA_last = (A)sh.coefA[p - 1];  // multiplies u_j
+    const A cA_last = ccoefA(p - 1);  // multiplies u_j
     bool gB[NBMAX], gA[NBMAX];
 #pragma unroll
     for (int g = 0; g < NBMAX; ++g) {
       gB[g] = EXTRA && ghost_active(g, j);
       gA[g] = EXTRA && ghost_active(g, j + 1);
-      cgb[g] = gB[g] ? (A)sh.cgB[g] : (A)0;
+      cgb[g] = gB[g] ? ccgB(g) : (A)0;
     }
     V* wout = uslot(j + p);
     const V* wcur = wslot(t);
     V* wnext = wslot(t + 1 < p ? t + 1 : t);
-    A an = 0, aw1 = 0, adot[PM], agr[PM], accb[NBA], agh[EXTRA ? NBMAX : 1];
+    R an{}, aw1{}, adot[PM], agr[PM], accb[NBA], agh[EXTRA ? NBMAX : 1];
 #pragma unroll
-    for (int k = 0; k < PM; ++k) adot[k] = agr[k] = 0;
+    for (int k = 0; k < PM; ++k) adot[k] = agr[k] = R{};
 #pragma unroll
-    for (int b = 0; b < NBA; ++b) accb[b] = 0;
+    for (int b = 0; b < NBA; ++b) accb[b] = R{};
 #pragma unroll
-    for (int g = 0; g < (EXTRA ? NBMAX : 1); ++g) agh[g] = 0;
+    for (int g = 0; g < (EXTRA ? NBMAX : 1); ++g) agh[g] = R{};
     if (warp == 1) {  // copy list: w'_j, u_j .. u_{j+p-1}, bench, then (A step) W_{t+1}, u_{j+1-p+k}
       const int n = 1 + p + nbp + (hasA ? p - ka : 0);
       for (int c = lane; c < n; c += 32) {
@@ -859,20 +875,20 @@ struct Engine {
       }
       vst<GG>(wout + r, w);
 #pragma unroll
-      for (int e = 0; e < GG; ++e) an += w[e] * w[e];
+      for (int e = 0; e < GG; ++e) dot_add(an, w[e], w[e]);
 #pragma unroll
       for (int k = 1; k < PM; ++k)
         if (k < p) {
           sld<GG>(sp + (SUB + k) * T, x);
 #pragma unroll
-          for (int e = 0; e < GG; ++e) agr[k - 1] += w[e] * x[e];
+          for (int e = 0; e < GG; ++e) dot_add(agr[k - 1], w[e], x[e]);
         }
 #pragma unroll
       for (int b = 0; b < NBPRE; ++b)
         if (b < nbp) {
           sld<GG>(sp + (SBN + b) * T, x);
 #pragma unroll
-          for (int e = 0; e < GG; ++e) accb[b] += x[e] * w[e];
+          for (int e = 0; e < GG; ++e) dot_add(accb[b], x[e], w[e]);
         }
       if constexpr (EXTRA) {
 #pragma unroll
@@ -880,7 +896,7 @@ struct Engine {
           if (b0 + b < nb) {
             vld<GG>(bench(b0 + b) + r, x);
 #pragma unroll
-            for (int e = 0; e < GG; ++e) accb[b] += x[e] * w[e];
+            for (int e = 0; e < GG; ++e) dot_add(accb[b], x[e], w[e]);
           }
       }
       // A step of j+1
@@ -888,7 +904,7 @@ struct Engine {
         A w1[GG];
         sld<GG>(sp + SW1 * T, w1);
 #pragma unroll
-        for (int e = 0; e < GG; ++e) aw1 += w1[e] * w1[e];
+        for (int e = 0; e < GG; ++e) dot_add(aw1, w1[e], w1[e]);
 #pragma unroll
         for (int k = 0; k < PM - 1; ++k)
           if (k < p - 1 && k >= ka) {
@@ -904,17 +920,17 @@ struct Engine {
           if (k < p - 1) {
             sld<GG>(sp + (SUB + k + 1) * T, x);
 #pragma unroll
-            for (int e = 0; e < GG; ++e) adot[k] += x[e] * w1[e];
+            for (int e = 0; e < GG; ++e) dot_add(adot[k], x[e], w1[e]);
           }
 #pragma unroll
-        for (int e = 0; e < GG; ++e) adot[PM - 1] += w[e] * w1[e];
+        for (int e = 0; e < GG; ++e) dot_add(adot[PM - 1], w[e], w1[e]);
         if constexpr (EXTRA) {
 #pragma unroll
           for (int g = 0; g < NBMAX; ++g)
             if (gA[g]) {
               vld<GG>(ghostv(g) + r, x);
 #pragma unroll
-              for (int e = 0; e < GG; ++e) agh[g] += x[e] * w1[e];
+              for (int e = 0; e < GG; ++e) dot_add(agh[g], x[e], w1[e]);
             }
         }
         vst<GG>(wnext + r, w1);
@@ -922,7 +938,7 @@ struct Engine {
     };
     const bool ok = tiles<T, G>(issue, body);
 #pragma unroll
-    for (int k = 0; k < LY::BA_N; ++k) acc[k] = 0;
+    for (int k = 0; k < LY::BA_N; ++k) acc[k] = R{};
     if constexpr (EXTRA) {
 #pragma unroll
       for (int g = 0; g < NBMAX; ++g) acc[LY::BA_GH + g] = agh[g];
@@ -948,7 +964,7 @@ struct Engine {
   //     vectors active at j+1.  Also ||w_j||^2, ||W_{t+1}||^2, w_j . u_{j+k} (Gram entries) and
   //     bench . w_j.  The control warp runs the QR step of iteration qr_j (if > 0) meanwhile.
   __device__ bool pass_ba(int j, int t, bool hasA, int qr_j, int qr_l) {
-    A acc[LY::BA_N];  // written after the streaming loop (not live across it)
+    R acc[LY::BA_N];  // written after the streaming loop (not live across it)
     int ng = 0;
 #pragma unroll
     for (int g = 0; g < NBMAX; ++g)
@@ -957,7 +973,7 @@ struct Engine {
     if (warp == 0) {
       if (qr_j > 0) qr_warp(qr_j, qr_l);
 #pragma unroll
-      for (int k = 0; k < LY::BA_N; ++k) acc[k] = 0;
+      for (int k = 0; k < LY::BA_N; ++k) acc[k] = R{};
     } else if (ng > 0 || nb - sh.bench_next > NBPRE) {
       ba_stream<true>(j, t, hasA, acc);  // removed vectors active, or many bench vectors
     } else {
@@ -1145,6 +1161,15 @@ struct Engine {
     sh.bc[b][par][l] = v;
     sh.bcf[b][par][l] = (float)v;
   }
+  __device__ __forceinline__ A ccoefA(int k) const {
+    if constexpr (sizeof(A) == 4) return sh.coefAf[k]; else return sh.coefA[k];
+  }
+  __device__ __forceinline__ A ccoefB(int k) const {
+    if constexpr (sizeof(A) == 4) return sh.coefBf[k]; else return sh.coefB[k];
+  }
+  __device__ __forceinline__ A ccgB(int g) const {
+    if constexpr (sizeof(A) == 4) return sh.cgBf[g]; else return sh.cgB[g];
+  }
   __device__ __forceinline__ A cdirA(int l) const {
     if constexpr (sizeof(A) == 4) return sh.dirAf[l]; else return sh.dirA[l];
   }
@@ -1319,6 +1344,7 @@ struct Engine {
     if (lane < p) {
       const int i = jn - p + lane;
       sh.coefA[lane] = (i >= 1) ? sh.hsub[i % p][jn - i - 1] * sig(i) : 0.0;
+      sh.coefAf[lane] = (float)sh.coefA[lane];
     }
   }
 
@@ -1332,6 +1358,7 @@ struct Engine {
       else
         sh.hsub[jn % p][lane - 1] = h;
       sh.coefB[lane] = h * sig(jn + lane);
+      sh.coefBf[lane] = (float)sh.coefB[lane];
     }
   }
 
@@ -1361,7 +1388,10 @@ struct Engine {
           (lane < p - 1) ? sh.rba[LY::BA_DOT + lane] : ((lane == p - 1) ? sh.rba[LY::BA_DOT + PM - 1] : 0.0);
       __syncwarp();
       ctl_astep(jj + 1, dr);
-      if (lane < NBMAX) sh.cgB[lane] = (lane < sh.n_ghost) ? sh.rba[LY::BA_GH + lane] : 0.0;
+      if (lane < NBMAX) {
+        sh.cgB[lane] = (lane < sh.n_ghost) ? sh.rba[LY::BA_GH + lane] : 0.0;
+        sh.cgBf[lane] = (float)sh.cgB[lane];
+      }
       if (lane == 0) sh.normAu2[(jj + 1) & 1] = sh.rba[LY::BA_W1];
       __syncwarp();
       if (t + 1 < p - 1) ctl_coefA(jj + 2);
@@ -1618,7 +1648,10 @@ struct Engine {
       if (warp == 0) {  // results of the A step of j0, known coefficients of j0+1
         const double dr = (lane < p) ? sh.red[LY::SP_DOT + lane] : 0.0;
         ctl_astep(j0, dr);
-        if (lane < NBMAX) sh.cgB[lane] = (lane < sh.n_ghost) ? sh.red[LY::SP_GH + lane] : 0.0;
+        if (lane < NBMAX) {
+          sh.cgB[lane] = (lane < sh.n_ghost) ? sh.red[LY::SP_GH + lane] : 0.0;
+          sh.cgBf[lane] = (float)sh.cgB[lane];
+        }
         if (lane == 0) sh.normAu2[j0 & 1] = sh.red[LY::SP_NRM];
         __syncwarp();
         if (p > 1) ctl_coefA(j0 + 1);
@@ -1726,8 +1759,7 @@ struct Engine {
 
 template <typename V, int PM, int NT>
 constexpr size_t solve_smem_bytes() {
-  static_assert(Tiles<V, PM, NT>::STG * Tiles<V, PM, NT>::NSTAGE >= sizeof(V) * (size_t)16 * (NT - 32),
-                "reduction scratch");
+  static_assert(Tiles<V, PM, NT>::STG * Tiles<V, PM, NT>::NSTAGE >= (size_t)8 * 16 * (NT - 32), "reduction scratch");
   return Tiles<V, PM, NT>::smem_bytes();
 }
 
