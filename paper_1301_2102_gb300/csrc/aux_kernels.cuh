@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "dword.cuh"
+
 namespace bmr {
 
 constexpr int AUX_NT = 256;
@@ -115,18 +117,24 @@ static __global__ void __launch_bounds__(AUX_NT) sddmm_kernel(int64_t n, int p, 
   }
 }
 
-// X += D (FP64 += FP32), row-major n x p, and D = 0.
-static __global__ void add_correction_kernel(int64_t total, double* X, float* D) {
+__device__ __forceinline__ double as_double(double x) { return x; }
+__device__ __forceinline__ double as_double(float x) { return (double)x; }
+__device__ __forceinline__ double as_double(dw x) { return to_double(x); }
+
+// X += D (FP64 += inner vector type), row-major n x p, and D = 0.
+template <typename V>
+__global__ void add_correction_kernel(int64_t total, double* X, V* D) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    X[i] += (double)D[i];
-    D[i] = 0.0f;
+    X[i] += as_double(D[i]);
+    D[i] = V(0);
   }
 }
 
-// FP32 copy of the matrix values.
-static __global__ void to_float_kernel(int64_t total, const double* a, float* b) {
+// Copy of the matrix values in the inner vector type (rounded to nearest).
+template <typename V>
+__global__ void to_vec_kernel(int64_t total, const double* a, V* b) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
+    b[i] = V(a[i]);
 }
 
 }  // namespace bmr

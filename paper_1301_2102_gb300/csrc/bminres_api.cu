@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -31,7 +32,7 @@ struct Workspace {
   void* Bench = nullptr;
   void* Ghost = nullptr;
   void* F = nullptr;
-  float* D = nullptr;     // mixed: correction, row-major n x p
+  void* D = nullptr;      // mixed: correction, row-major n x p, inner vector type
   double* part = nullptr; // reductions of the persistent kernel
   double* npart = nullptr;// residual-norm partials
   double* norms = nullptr;// p norms (device)
@@ -49,7 +50,8 @@ struct bminres_handle_s {
   int32_t* rowptr = nullptr;
   int32_t* colidx = nullptr;
   double* vals = nullptr;
-  float* vals32 = nullptr;
+  float* vals32 = nullptr;   // FP32 copy of the values (MIXED)
+  bmr::dw* vals_dw = nullptr; // double-word copy of the values (MIXED_DW)
   bmr::Ctl* ctl = nullptr;      // device
   bmr::Ctl* ctl_host = nullptr; // pinned
   double* norms_host = nullptr; // pinned, 2 * 32
@@ -97,6 +99,11 @@ int pm_for(int p) {
 
 int64_t padded_ld(int64_t n) { return (n + 63) / 64 * 64; }
 
+// largest block size with a kernel instantiation for vector type V (double-word: 16, the
+// coefficient copies of p = 32 leave too little shared memory for staging)
+template <typename V>
+constexpr int pmax_of() { return std::is_same<V, bmr::dw>::value ? 16 : 32; }
+
 template <typename V>
 int blocks_per_sm(int pm) {
   switch (pm) {
@@ -105,7 +112,8 @@ int blocks_per_sm(int pm) {
     case 4: return bmr::SolveLauncher<V, 4>::blocks_per_sm();
     case 8: return bmr::SolveLauncher<V, 8>::blocks_per_sm();
     case 16: return bmr::SolveLauncher<V, 16>::blocks_per_sm();
-    case 32: return bmr::SolveLauncher<V, 32>::blocks_per_sm();
+    case 32:
+      if constexpr (pmax_of<V>() >= 32) return bmr::SolveLauncher<V, 32>::blocks_per_sm();
   }
   return 0;
 }
@@ -117,7 +125,8 @@ cudaError_t launch_solve(int pm, const bmr::SolveArgs<V>& a, int grid, cudaStrea
     case 4: return bmr::SolveLauncher<V, 4>::launch(a, grid, s);
     case 8: return bmr::SolveLauncher<V, 8>::launch(a, grid, s);
     case 16: return bmr::SolveLauncher<V, 16>::launch(a, grid, s);
-    case 32: return bmr::SolveLauncher<V, 32>::launch(a, grid, s);
+    case 32:
+      if constexpr (pmax_of<V>() >= 32) return bmr::SolveLauncher<V, 32>::launch(a, grid, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -134,8 +143,8 @@ int nvmax_for(int pm) {
 }
 
 // grid of the persistent kernel: one wave of co-resident blocks, fewer for small n
-int solve_grid(bminres_handle h, int pm, bool f32) {
-  int bps = f32 ? blocks_per_sm<float>(pm) : blocks_per_sm<double>(pm);
+int solve_grid(bminres_handle h, int pm, int prec) {
+  int bps = prec == 1 ? blocks_per_sm<float>(pm) : (prec == 2 ? blocks_per_sm<bmr::dw>(pm) : blocks_per_sm<double>(pm));
   if (bps <= 0) return 0;
   int64_t full = (int64_t)bps * h->num_sms;
   int64_t want = (h->n + 511) / 512;  // at least two rows per thread and pass
@@ -149,12 +158,17 @@ void free_ws(bmr::Workspace& w) {
   w = bmr::Workspace();
 }
 
-// (Re)allocate the workspace for block size p and precision prec (0 = FP64, 1 = FP32 vectors).
+// vector precision of the solves of a handle: 0 = FP64, 1 = FP32, 2 = double-word
+int prec_of(bminres_handle h) {
+  return h->opts.precision == BMINRES_MIXED ? 1 : (h->opts.precision == BMINRES_MIXED_DW ? 2 : 0);
+}
+
+// (Re)allocate the workspace for block size p and vector precision prec (see prec_of).
 bminres_status ensure_ws(bminres_handle h, int p, int prec) {
   bmr::Workspace& w = h->ws;
   const int pm = pm_for(p);
   const bool f32 = (prec == 1);
-  const int grid = solve_grid(h, pm, f32);
+  const int grid = solve_grid(h, pm, prec);
   if (grid <= 0) return BMINRES_ERR_CUDA;
   if (w.base && w.p == p && w.prec == prec && w.grid == grid) return BMINRES_OK;
   free_ws(w);
@@ -170,7 +184,7 @@ bminres_status ensure_ws(bminres_handle h, int p, int prec) {
   size_t oB = off; off += al(nb * ld * es);
   size_t oG = off; off += al(nb * ld * es);
   size_t oF = off; off += al(p * ld * es);
-  size_t oD = off; off += f32 ? al((size_t)h->n * p * sizeof(float)) : 0;
+  size_t oD = off; off += prec != 0 ? al((size_t)h->n * p * es) : 0;
   size_t oP = off; off += al((size_t)2 * nvmax_for(pm) * grid * sizeof(double));
   const int nres = (int)((h->n + bmr::AUX_NT - 1) / bmr::AUX_NT);
   size_t oN = off; off += al((size_t)p * std::max(nres, 1) * sizeof(double));
@@ -196,7 +210,7 @@ bminres_status ensure_ws(bminres_handle h, int p, int prec) {
   w.Bench = b + oB;
   w.Ghost = b + oG;
   w.F = b + oF;
-  w.D = f32 ? (float*)(b + oD) : nullptr;
+  w.D = prec != 0 ? (void*)(b + oD) : nullptr;
   w.part = (double*)(b + oP);
   w.npart = (double*)(b + oN);
   w.norms = (double*)(b + oNo);
@@ -232,8 +246,13 @@ bminres_status residual(bminres_handle h, int p, const double* B, const double* 
 // dependent vector, so an FP32 inner solve cannot resolve gamma below ~1e-5.
 template <typename V>
 double effective_gamma(double gamma) {
-  return sizeof(V) == sizeof(float) ? std::max(gamma, 1e-5) : gamma;
+  return std::is_same<V, float>::value ? std::max(gamma, 1e-5) : gamma;
 }
+
+template <typename V> const V* vals_of(bminres_handle h);
+template <> const double* vals_of<double>(bminres_handle h) { return h->vals; }
+template <> const float* vals_of<float>(bminres_handle h) { return h->vals32; }
+template <> const bmr::dw* vals_of<bmr::dw>(bminres_handle h) { return h->vals_dw; }
 
 template <typename V>
 bminres_status persistent_solve(bminres_handle h, int p, V* Xout, double tol, int maxit, cudaStream_t s,
@@ -308,20 +327,72 @@ bminres_status map_kernel_status(int st) {
   return BMINRES_ERR_CUDA;
 }
 
+// FP64 iterative refinement around inner block MINRES solves with vectors of type V (FP32 or
+// double-word): R = B - A X in FP64 (stored as V), solve A D = R to opts.tol_inner, X += D, until
+// the FP64 residual meets tol.  f0 receives the initial residual norms.
+template <typename V>
+bminres_status refine(bminres_handle h, int p, const double* B, double* X, double tol, int maxit, cudaStream_t s,
+                      double* f0, bminres_info& inf) {
+  bmr::Workspace& w = h->ws;
+  V* D = (V*)w.D;
+  BMR_TRY(cudaMemsetAsync(D, 0, sizeof(V) * h->n * p, s));
+  bminres_status st = BMINRES_NOT_CONVERGED;
+  int used = 0;
+  for (int outer = 0; outer < h->opts.max_outer; ++outer) {
+    bminres_status rs = residual<V>(h, p, B, X, (V*)w.F, s, true);
+    if (rs != BMINRES_OK) return rs;
+    if (outer == 0)
+      for (int i = 0; i < p; ++i) f0[i] = h->norms_host[i];
+    double worst = 0.0;
+    for (int i = 0; i < p; ++i) worst = std::max(worst, f0[i] > 0 ? h->norms_host[i] / f0[i] : 0.0);
+    inf.relres_true_max = worst;
+    if (worst < tol) {
+      st = BMINRES_OK;
+      break;
+    }
+    if (used >= maxit) break;
+    Ctl r;
+    rs = persistent_solve<V>(h, p, D, h->opts.tol_inner, maxit - used, s, vals_of<V>(h), &r, &inf.kernel_ms);
+    if (rs != BMINRES_OK) return rs;
+    used += r.iters;
+    inf.iters += r.iters;
+    inf.cycles += r.cycles;
+    inf.outer = outer + 1;
+    inf.deflations += r.deflations;
+    inf.setup_deflations += r.setup_deflations;
+    inf.bench_used = std::max(inf.bench_used, r.bench_used);
+    inf.relres_est_max = r.relres_est_max;
+    add_timeline(inf, r);
+    bminres_status ks = map_kernel_status(r.status);
+    if (ks != BMINRES_OK && ks != BMINRES_NOT_CONVERGED) {
+      st = ks;
+      break;
+    }
+    const int64_t total = h->n * p;
+    bmr::add_correction_kernel<V><<<std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4096)), 256, 0, s>>>(
+        total, X, D);
+    BMR_TRY(cudaGetLastError());
+    h->launches++;
+    if (r.iters == 0) break;  // inner solve could not make progress
+  }
+  return st;
+}
+
 // The solve on device-resident B and X.
 bminres_status solve_device(bminres_handle h, int p, const double* B, double* X, double tol, int maxit,
                             cudaStream_t s, double* relres_true, bminres_info* info) {
   bminres_info inf;
   memset(&inf, 0, sizeof(inf));
   h->launches = 0;
-  const bool mixed = (h->opts.precision == BMINRES_MIXED);
-  bminres_status st = ensure_ws(h, p, mixed ? 1 : 0);
+  const int prec = prec_of(h);
+  if (prec == 2 && p > pmax_of<bmr::dw>()) return BMINRES_ERR_INVALID;
+  bminres_status st = ensure_ws(h, p, prec);
   if (st != BMINRES_OK) return st;
   bmr::Workspace& w = h->ws;
   inf.grid_blocks = w.grid;
   double f0[PMAX];
   BMR_TRY(cudaEventRecord(h->ev0, s));
-  if (!mixed) {
+  if (prec == 0) {
     st = residual<double>(h, p, B, X, (double*)w.F, s, true);
     if (st != BMINRES_OK) return st;
     for (int i = 0; i < p; ++i) f0[i] = h->norms_host[i];
@@ -337,54 +408,17 @@ bminres_status solve_device(bminres_handle h, int p, const double* B, double* X,
     inf.relres_est_max = r.relres_est_max;
     add_timeline(inf, r);
     st = map_kernel_status(r.status);
+  } else if (prec == 1) {
+    st = refine<float>(h, p, B, X, tol, maxit, s, f0, inf);
   } else {
-    // FP64 iterative refinement around FP32 inner block MINRES solves
-    BMR_TRY(cudaMemsetAsync(w.D, 0, sizeof(float) * h->n * p, s));
-    st = BMINRES_NOT_CONVERGED;
-    int used = 0;
-    for (int outer = 0; outer < h->opts.max_outer; ++outer) {
-      bminres_status rs = residual<float>(h, p, B, X, (float*)w.F, s, true);
-      if (rs != BMINRES_OK) return rs;
-      if (outer == 0)
-        for (int i = 0; i < p; ++i) f0[i] = h->norms_host[i];
-      double worst = 0.0;
-      for (int i = 0; i < p; ++i) worst = std::max(worst, f0[i] > 0 ? h->norms_host[i] / f0[i] : 0.0);
-      inf.relres_true_max = worst;
-      if (worst < tol) {
-        st = BMINRES_OK;
-        break;
-      }
-      if (used >= maxit) break;
-      Ctl r;
-      rs = persistent_solve<float>(h, p, w.D, h->opts.tol_inner, maxit - used, s, h->vals32, &r, &inf.kernel_ms);
-      if (rs != BMINRES_OK) return rs;
-      used += r.iters;
-      inf.iters += r.iters;
-      inf.cycles += r.cycles;
-      inf.outer = outer + 1;
-      inf.deflations += r.deflations;
-      inf.setup_deflations += r.setup_deflations;
-      inf.bench_used = std::max(inf.bench_used, r.bench_used);
-      inf.relres_est_max = r.relres_est_max;
-      add_timeline(inf, r);
-      bminres_status ks = map_kernel_status(r.status);
-      if (ks != BMINRES_OK && ks != BMINRES_NOT_CONVERGED) {
-        st = ks;
-        break;
-      }
-      const int64_t total = h->n * p;
-      bmr::add_correction_kernel<<<std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4096)), 256, 0, s>>>(
-          total, X, w.D);
-      BMR_TRY(cudaGetLastError());
-      h->launches++;
-      if (r.iters == 0) break;  // inner solve could not make progress
-    }
+    st = refine<bmr::dw>(h, p, B, X, tol, maxit, s, f0, inf);
   }
   // FP64 true residual of the result
   st = (st == BMINRES_OK || st == BMINRES_NOT_CONVERGED) ? st : st;
   {
-    bminres_status rs = mixed ? residual<float>(h, p, B, X, (float*)w.F, s, true)
-                              : residual<double>(h, p, B, X, (double*)w.F, s, true);
+    bminres_status rs = prec == 1   ? residual<float>(h, p, B, X, (float*)w.F, s, true)
+                        : prec == 2 ? residual<bmr::dw>(h, p, B, X, (bmr::dw*)w.F, s, true)
+                                    : residual<double>(h, p, B, X, (double*)w.F, s, true);
     if (rs != BMINRES_OK) return rs;
     double worst = 0.0;
     for (int i = 0; i < p; ++i) {
@@ -446,7 +480,7 @@ bminres_status bminres_create(bminres_handle* out, int64_t n, int64_t nnz, const
   bminres_opts o;
   bminres_default_opts(&o);
   if (opts) o = *opts;
-  if (o.bench < 0 || o.bench > bmr::NBMAX || !(o.gamma >= 0.0) || (o.precision != BMINRES_FP64 && o.precision != BMINRES_MIXED))
+  if (o.bench < 0 || o.bench > bmr::NBMAX || !(o.gamma >= 0.0) || (o.precision != BMINRES_FP64 && o.precision != BMINRES_MIXED && o.precision != BMINRES_MIXED_DW))
     return BMINRES_ERR_INVALID;
   if (o.max_outer <= 0) o.max_outer = 20;
   if (!(o.tol_inner > 0.0)) o.tol_inner = 1e-5;
@@ -493,7 +527,12 @@ bminres_status bminres_create(bminres_handle* out, int64_t n, int64_t nnz, const
   if (cudaMalloc(&h->rowptr, sizeof(int32_t) * (n + 1)) != cudaSuccess) return fail(BMINRES_ERR_OOM);
   if (cudaMalloc(&h->colidx, sizeof(int32_t) * std::max<int64_t>(nnz, 1)) != cudaSuccess) return fail(BMINRES_ERR_OOM);
   if (cudaMalloc(&h->vals, sizeof(double) * std::max<int64_t>(nnz, 1)) != cudaSuccess) return fail(BMINRES_ERR_OOM);
-  if (cudaMalloc(&h->vals32, sizeof(float) * std::max<int64_t>(nnz, 1)) != cudaSuccess) return fail(BMINRES_ERR_OOM);
+  if (o.precision == BMINRES_MIXED &&
+      cudaMalloc(&h->vals32, sizeof(float) * std::max<int64_t>(nnz, 1)) != cudaSuccess)
+    return fail(BMINRES_ERR_OOM);
+  if (o.precision == BMINRES_MIXED_DW &&
+      cudaMalloc(&h->vals_dw, sizeof(bmr::dw) * std::max<int64_t>(nnz, 1)) != cudaSuccess)
+    return fail(BMINRES_ERR_OOM);
   if (cudaMalloc(&h->ctl, sizeof(Ctl)) != cudaSuccess) return fail(BMINRES_ERR_OOM);
   if (cudaMallocHost(&h->ctl_host, sizeof(Ctl)) != cudaSuccess) return fail(BMINRES_ERR_OOM);
   if (cudaMallocHost(&h->norms_host, sizeof(double) * 64) != cudaSuccess) return fail(BMINRES_ERR_OOM);
@@ -523,8 +562,15 @@ bminres_status bminres_set_values(bminres_handle h, const double* vals, bminres_
   if (!vals) return BMINRES_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   BMR_TRY(cudaMemcpyAsync(h->vals, vals, sizeof(double) * h->nnz, cudaMemcpyDefault, s));
-  bmr::to_float_kernel<<<(int)std::min<int64_t>((h->nnz + 255) / 256, 4096), 256, 0, s>>>(h->nnz, h->vals, h->vals32);
-  BMR_TRY(cudaGetLastError());
+  const int cb = (int)std::min<int64_t>((h->nnz + 255) / 256, 4096);
+  if (h->vals32) {
+    bmr::to_vec_kernel<float><<<cb, 256, 0, s>>>(h->nnz, h->vals, h->vals32);
+    BMR_TRY(cudaGetLastError());
+  }
+  if (h->vals_dw) {
+    bmr::to_vec_kernel<bmr::dw><<<cb, 256, 0, s>>>(h->nnz, h->vals, h->vals_dw);
+    BMR_TRY(cudaGetLastError());
+  }
   BMR_TRY(cudaStreamSynchronize(s));
   return BMINRES_OK;
 }
@@ -536,6 +582,7 @@ void bminres_destroy(bminres_handle h) {
   if (h->colidx) cudaFree(h->colidx);
   if (h->vals) cudaFree(h->vals);
   if (h->vals32) cudaFree(h->vals32);
+  if (h->vals_dw) cudaFree(h->vals_dw);
   if (h->ctl) cudaFree(h->ctl);
   if (h->ctl_host) cudaFreeHost(h->ctl_host);
   if (h->norms_host) cudaFreeHost(h->norms_host);
@@ -557,7 +604,7 @@ bminres_status bminres_solve(bminres_handle h, int p, const double* B, double* X
   const bool dB = is_device_ptr(B), dX = is_device_ptr(X);
   if (dB && dX) return solve_device(h, p, B, X, tol, maxit, s, relres_true, info);
   // host buffers: stage through handle-owned device memory (copies are part of the call)
-  bminres_status st = ensure_ws(h, p, h->opts.precision == BMINRES_MIXED ? 1 : 0);
+  bminres_status st = ensure_ws(h, p, prec_of(h));
   if (st != BMINRES_OK) return st;
   const size_t bytes = sizeof(double) * h->n * p;
   double* Bd = dB ? (double*)B : h->ws.Btmp;

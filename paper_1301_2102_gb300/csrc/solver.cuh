@@ -39,6 +39,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "dword.cuh"
 
 namespace bmr {
 
@@ -87,7 +88,14 @@ struct Layout {
 constexpr int NSTAGE_MAX = 2;  // staging buffers of the streaming passes (fewer for p > 16)
 constexpr int TQMAX = 512;  // tiles per block whose CSR offsets are tabulated for the block product
 
-template <int PM>
+// Element type of the coefficient copies read by the streaming passes: the vector element type for
+// FP32 and double-word vectors (so that the row loops convert nothing), unused for FP64 vectors.
+template <typename V> struct CoefCopy { using T = V; };
+template <> struct CoefCopy<double> { using T = unsigned char; };
+template <typename CT> __device__ __forceinline__ CT to_coef(double d) { return (CT)d; }
+template <> __device__ __forceinline__ unsigned char to_coef<unsigned char>(double) { return 0; }
+
+template <int PM, typename CT>
 struct __align__(16) Shared {
   unsigned long long tbar[NSTAGE_MAX];  // completion barriers of the staging buffers
   unsigned long long bar_epoch;         // grid barriers this block has passed (thread 0)
@@ -131,10 +139,10 @@ struct __align__(16) Shared {
     double S[PM][PM];           // initial QR factor
   };
   double qd[PM], qe[PM];        // set-up Gram-Schmidt coefficients
-  // single-precision copies of the direction-pass coefficients (used by FP32 vectors, so that the
-  // row loop does no double -> float conversions, which run on the slow FP64 pipe)
-  float dirAf[PM], dirBf[PM][2 * PM], Zcf[PM][PM], bcf[NBMAX][2][PM];
-  float coefAf[PM], coefBf[PM], cgBf[NBMAX];  // single-precision copies of coefA, coefB, cgB
+  // copies of the coefficients read in the row loops, in the vector element type (conversions from
+  // double run on the slow FP64 pipe of GB300, so they are done once, by the control warp)
+  CT dirAc[PM], dirBc[PM][2 * PM], Zcc[PM][PM], bcc[NBMAX][2][PM];
+  CT coefAc[PM], coefBc[PM], cgBc[NBMAX];
   double red[Layout<PM>::NVMAX];   // values of the last grid reduction
   double rba[Layout<PM>::NVMAX];   // saved values of the last fused pass
   double s2[Layout<PM>::NVMAX][32];
@@ -151,7 +159,16 @@ template <int G, typename V>
 __device__ __forceinline__ void vld(const V* p, V (&x)[G]) {
   static_assert(G == 1 || G == 2 || G == 4, "group width");
   static_assert(G * sizeof(V) <= 16, "group wider than 16 bytes");
-  if constexpr (G == 1) {
+  if constexpr (std::is_same<V, dw>::value) {
+    if constexpr (G == 1) {
+      const float2 t = *reinterpret_cast<const float2*>(p);
+      x[0] = dw::make(t.x, t.y);
+    } else {
+      const float4 t = *reinterpret_cast<const float4*>(p);
+      x[0] = dw::make(t.x, t.y);
+      x[1] = dw::make(t.z, t.w);
+    }
+  } else if constexpr (G == 1) {
     x[0] = *p;
   } else if constexpr (sizeof(V) == 8) {
     const double2 t = *reinterpret_cast<const double2*>(p);
@@ -172,7 +189,12 @@ __device__ __forceinline__ void vld(const V* p, V (&x)[G]) {
 
 template <int G, typename V>
 __device__ __forceinline__ void vst(V* p, const V (&x)[G]) {
-  if constexpr (G == 1) {
+  if constexpr (std::is_same<V, dw>::value) {
+    if constexpr (G == 1)
+      *reinterpret_cast<float2*>(p) = make_float2(x[0].hi, x[0].lo);
+    else
+      *reinterpret_cast<float4*>(p) = make_float4(x[0].hi, x[0].lo, x[1].hi, x[1].lo);
+  } else if constexpr (G == 1) {
     *p = x[0];
   } else if constexpr (sizeof(V) == 8) {
     *reinterpret_cast<double2*>(p) = make_double2(x[0], x[1]);
@@ -208,6 +230,29 @@ __device__ __forceinline__ void sld(const double* p, double (&x)[G]) {
   }
 }
 
+template <int G>
+__device__ __forceinline__ void sld(const dw* p, dw (&x)[G]) {
+  const unsigned a = smem_u32(p);
+  float h0, l0, h1, l1;
+  if constexpr (G == 1) {
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(h0), "=f"(l0) : "r"(a));
+    x[0] = dw::make(h0, l0);
+  } else {
+    static_assert(G == 2, "group width");
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(h0), "=f"(l0), "=f"(h1), "=f"(l1) : "r"(a));
+    x[0] = dw::make(h0, l0);
+    x[1] = dw::make(h1, l1);
+  }
+}
+
+// one CSR value through the read-only path
+__device__ __forceinline__ double ldg_val(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ldg_val(const float* p) { return __ldg(p); }
+__device__ __forceinline__ dw ldg_val(const dw* p) {
+  const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+  return dw::make(t.x, t.y);
+}
+
 // Per-thread accumulation of inner products (a += x * y), block-level sums (a += b) and the FP64
 // value of an accumulator, for every vector element type.
 __device__ __forceinline__ void dot_add(double& a, double x, double y) { a = fma(x, y, a); }
@@ -216,6 +261,9 @@ __device__ __forceinline__ void dot_sum(double& a, double b) { a += b; }
 __device__ __forceinline__ void dot_sum(float& a, float b) { a += b; }
 __device__ __forceinline__ double dot_val(double a) { return a; }
 __device__ __forceinline__ double dot_val(float a) { return (double)a; }
+__device__ __forceinline__ void dot_add(dw& a, dw x, dw y) { a = dw_add(a, dw_mul(x, y)); }
+__device__ __forceinline__ void dot_sum(dw& a, dw b) { a = dw_add(a, b); }
+__device__ __forceinline__ double dot_val(dw a) { return to_double(a); }
 
 // Shared-memory staging of the streaming passes: NSTAGE buffers of STG bytes after the Shared block
 // (the reduction scratch reuses them).  A pass that streams `nsl` vector slots per row works on
@@ -224,7 +272,7 @@ template <typename V, int PM, int NT>
 struct Tiles {
   static constexpr int NS = NT - 32;
   static constexpr int NSTAGE = PM > 16 ? 2 : NSTAGE_MAX;
-  static constexpr size_t SH = (sizeof(Shared<PM>) + 127) / 128 * 128;
+  static constexpr size_t SH = (sizeof(Shared<PM, typename CoefCopy<V>::T>) + 127) / 128 * 128;
   static constexpr size_t BUDGET = 227 * 1024 - 1024;  // dynamic shared memory of one block
   static constexpr size_t STG_MAX = 80 * 1024;
   static constexpr size_t STG =
@@ -270,7 +318,9 @@ struct Engine {
   static constexpr int RCH = 16;      // values per chunk of a block reduction
   static constexpr int NBPRE = 4;     // bench vectors held in registers by the fused pass
   const SolveArgs<V>& a;
-  Shared<PM>& sh;
+  using SHT = Shared<PM, typename CoefCopy<V>::T>;
+  using CT = typename CoefCopy<V>::T;
+  SHT& sh;
   using TL = Tiles<V, PM, NT>;
   A* scr;  // [RCH][NS] scratch for block reductions (inside the staging buffers)
   V* stg;  // staging buffers
@@ -282,7 +332,7 @@ struct Engine {
   int lane, warp;
   unsigned long long t_mark;
 
-  __device__ Engine(const SolveArgs<V>& args, Shared<PM>& s, V* scratch)
+  __device__ Engine(const SolveArgs<V>& args, SHT& s, V* scratch)
       : a(args), sh(s), scr(reinterpret_cast<A*>(scratch)), stg(scratch), tseq(0), buf(0), p(args.p), t_mark(0) {
     nblocks = gridDim.x;
     int64_t chunk = (a.n + nblocks - 1) / nblocks;
@@ -703,7 +753,7 @@ struct Engine {
                   cv[e][qq] = cvs[q - c.qa];
                 } else {
                   ci[e][qq] = __ldg(a.colidx + q);
-                  cv[e][qq] = (A)__ldg(a.vals + q);
+                  cv[e][qq] = ldg_val(a.vals + q);
                 }
               }
             }
@@ -1159,28 +1209,29 @@ struct Engine {
   // bench vectors lose their components along u_{j0} .. u_{j0+p-1} (coefficients of parity cyc).
   __device__ __forceinline__ void set_bc(int b, int par, int l, double v) {
     sh.bc[b][par][l] = v;
-    sh.bcf[b][par][l] = (float)v;
+    sh.bcc[b][par][l] = to_coef<CT>(v);
   }
+  static constexpr bool F64 = std::is_same<V, double>::value;
   __device__ __forceinline__ A ccoefA(int k) const {
-    if constexpr (sizeof(A) == 4) return sh.coefAf[k]; else return sh.coefA[k];
+    if constexpr (F64) return sh.coefA[k]; else return sh.coefAc[k];
   }
   __device__ __forceinline__ A ccoefB(int k) const {
-    if constexpr (sizeof(A) == 4) return sh.coefBf[k]; else return sh.coefB[k];
+    if constexpr (F64) return sh.coefB[k]; else return sh.coefBc[k];
   }
   __device__ __forceinline__ A ccgB(int g) const {
-    if constexpr (sizeof(A) == 4) return sh.cgBf[g]; else return sh.cgB[g];
+    if constexpr (F64) return sh.cgB[g]; else return sh.cgBc[g];
   }
   __device__ __forceinline__ A cdirA(int l) const {
-    if constexpr (sizeof(A) == 4) return sh.dirAf[l]; else return sh.dirA[l];
+    if constexpr (F64) return sh.dirA[l]; else return sh.dirAc[l];
   }
   __device__ __forceinline__ A cdirB(int l, int q) const {
-    if constexpr (sizeof(A) == 4) return sh.dirBf[l][q]; else return sh.dirB[l][q];
+    if constexpr (F64) return sh.dirB[l][q]; else return sh.dirBc[l][q];
   }
   __device__ __forceinline__ A cZ(int l, int c) const {
-    if constexpr (sizeof(A) == 4) return sh.Zcf[l][c]; else return sh.Zc[l][c];
+    if constexpr (F64) return sh.Zc[l][c]; else return sh.Zcc[l][c];
   }
   __device__ __forceinline__ A cbc(int b, int par, int l) const {
-    if constexpr (sizeof(A) == 4) return sh.bcf[b][par][l]; else return sh.bc[b][par][l];
+    if constexpr (F64) return sh.bc[b][par][l]; else return sh.bcc[b][par][l];
   }
 
   // Staged slots: m_{j0-2p} .. m_{j0-1}, u_{j0} .. u_{j0+p-1}, the iterate rows (p values per row,
@@ -1344,7 +1395,7 @@ struct Engine {
     if (lane < p) {
       const int i = jn - p + lane;
       sh.coefA[lane] = (i >= 1) ? sh.hsub[i % p][jn - i - 1] * sig(i) : 0.0;
-      sh.coefAf[lane] = (float)sh.coefA[lane];
+      sh.coefAc[lane] = to_coef<CT>(sh.coefA[lane]);
     }
   }
 
@@ -1358,7 +1409,7 @@ struct Engine {
       else
         sh.hsub[jn % p][lane - 1] = h;
       sh.coefB[lane] = h * sig(jn + lane);
-      sh.coefBf[lane] = (float)sh.coefB[lane];
+      sh.coefBc[lane] = to_coef<CT>(sh.coefB[lane]);
     }
   }
 
@@ -1390,7 +1441,7 @@ struct Engine {
       ctl_astep(jj + 1, dr);
       if (lane < NBMAX) {
         sh.cgB[lane] = (lane < sh.n_ghost) ? sh.rba[LY::BA_GH + lane] : 0.0;
-        sh.cgBf[lane] = (float)sh.cgB[lane];
+        sh.cgBc[lane] = to_coef<CT>(sh.cgB[lane]);
       }
       if (lane == 0) sh.normAu2[(jj + 1) & 1] = sh.rba[LY::BA_W1];
       __syncwarp();
@@ -1505,17 +1556,17 @@ struct Engine {
       const int qq = q - (2 * PM - P2);  // R row j-2p+qq
       const double dbq = (qq >= 0 && j - P2 + qq >= 1) ? -sh.y[qq] * rinvp : 0.0;
       sh.dirB[l][q] = dbq;
-      sh.dirBf[l][q] = (float)dbq;
+      sh.dirBc[l][q] = to_coef<CT>(dbq);
     }
     if (lane == 0) {
       sh.rjj[l] = sh.pref[p] * rinvp;
       sh.dirA[l] = sh.sigq * rinvp;
-      sh.dirAf[l] = (float)sh.dirA[l];
+      sh.dirAc[l] = to_coef<CT>(sh.dirA[l]);
     }
     bool conv = true, fin = true;
     if (lane < p) {
       sh.Zc[l][lane] = sh.Sh[j % (p + 1)][lane];
-      sh.Zcf[l][lane] = (float)sh.Zc[l][lane];
+      sh.Zcc[l][lane] = to_coef<CT>(sh.Zc[l][lane]);
       double s = 0.0;
       for (int k = 1; k <= p; ++k) {
         const double v = sh.Sh[(j + k) % (p + 1)][lane];
@@ -1554,7 +1605,7 @@ struct Engine {
     Ctl* ctl = a.ctl;
     const unsigned long long t_start = gtimer();
     t_mark = t_start;
-    for (int i = tid; i < (int)(sizeof(Shared<PM>) / 8); i += NT) reinterpret_cast<double*>(&sh)[i] = 0.0;
+    for (int i = tid; i < (int)(sizeof(SHT) / 8); i += NT) reinterpret_cast<double*>(&sh)[i] = 0.0;
     __syncthreads();
     if (tid == 0) {
       for (int k = 0; k < TL::NSTAGE; ++k) mbar_init(&sh.tbar[k], 1);
@@ -1650,7 +1701,7 @@ struct Engine {
         ctl_astep(j0, dr);
         if (lane < NBMAX) {
           sh.cgB[lane] = (lane < sh.n_ghost) ? sh.red[LY::SP_GH + lane] : 0.0;
-          sh.cgBf[lane] = (float)sh.cgB[lane];
+          sh.cgBc[lane] = to_coef<CT>(sh.cgB[lane]);
         }
         if (lane == 0) sh.normAu2[j0 & 1] = sh.red[LY::SP_NRM];
         __syncwarp();
@@ -1766,7 +1817,8 @@ constexpr size_t solve_smem_bytes() {
 template <typename V, int PM, int NT>
 __global__ void __launch_bounds__(NT, 1) bminres_solve_kernel(SolveArgs<V> args) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  Shared<PM>& sh = *reinterpret_cast<Shared<PM>*>(smem_raw);
+  using SHT = Shared<PM, typename CoefCopy<V>::T>;
+  SHT& sh = *reinterpret_cast<SHT*>(smem_raw);
   V* stg = reinterpret_cast<V*>(smem_raw + Tiles<V, PM, NT>::SH);
   Engine<V, PM, NT> e(args, sh, stg);
   e.run();

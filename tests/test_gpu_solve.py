@@ -162,6 +162,39 @@ def test_mixed_precision_reaches_tol(torch_cuda, oracle_mod, workloads):
     assert err < 1e-6, err
 
 
+@pytest.mark.parametrize("p", [1, 4, 8])
+def test_double_word_inner_solve_matches_oracle(torch_cuda, oracle_mod, workloads, p):
+    """One double-word inner solve (no refinement step) to a recursive 1e-10: the iterate agrees
+    with the FP64 oracle to the FP64 bar (1e-7 relative) and the band iteration count within the
+    finite-precision Lanczos bar, because ~48-bit vectors keep the recurrence close to FP64's."""
+    A = workloads.laplacian(24, 2, workloads.shift_at_fraction(24, 2, 0.15))
+    B = workloads.randn_rhs(A.n, p, 11)
+    ref = oracle_mod.bminres(A, B, tol=1e-10, maxit=20000)
+    X, info, rel = _solve(torch_cuda, A, B, maxit=20000, precision="mixed_dw", tol_inner=1e-10, max_outer=1)
+    assert info["outer"] == 1
+    assert iters_close(info["iters"], ref.iters), (info["iters"], ref.iters)
+    assert np.linalg.norm(X - ref.X) <= 1e-7 * np.linalg.norm(ref.X)
+
+
+def test_double_word_refinement_reaches_tol(torch_cuda, oracle_mod, workloads):
+    A = workloads.laplacian(16, 3, workloads.shift_at_fraction(16, 3, 0.1))
+    B = workloads.dependent_rhs_p8(A.n, seed=2)
+    ref = oracle_mod.bminres(A, B, tol=1e-10, maxit=40000)
+    X, info, rel = _solve(torch_cuda, A, B, maxit=200000, precision="mixed_dw")
+    assert info["status"] == 0, info
+    assert rel.max() < 1e-10 and info["setup_deflations"] == ref.setup_deflations
+    assert np.linalg.norm(X - ref.X) / np.linalg.norm(ref.X) < 1e-7
+
+
+def test_double_word_rejects_p_above_16(torch_cuda, workloads):
+    from paper_1301_2102_gb300 import Solver
+    from paper_1301_2102_gb300._lib import BminresError
+
+    A = workloads.laplacian(12, 2, 0.3)
+    with Solver(A, precision="mixed_dw") as s, pytest.raises(BminresError):
+        s.solve(torch_cuda.from_numpy(workloads.randn_rhs(A.n, 17, 0)).cuda(), tol=1e-8, maxit=100)
+
+
 @pytest.mark.parametrize("p", [1, 3, 8])
 def test_residual_history_matches_before_amplification(torch_cuda, oracle_mod, workloads, p):
     """Iterate-by-iterate parity: the recursive residual norms of every band iteration agree with
