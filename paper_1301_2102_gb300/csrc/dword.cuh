@@ -67,6 +67,23 @@ __device__ __forceinline__ dw dw_mul(dw x, dw y) {
   return dw::make(zh, zl);
 }
 
+// a * b + c for the streaming passes: the product of the high parts exactly (TwoProd), the cross
+// terms by FMA, then one error-free sum with c.hi and a Fast2Sum renormalisation (15 FP32
+// operations instead of 28 for dw_add(dw_mul)).  The error is a few u^2 (|a b| + |c|): under
+// cancellation it is absolute rather than relative, i.e. of the order of the rounding already
+// present in the double-word operands, which is what an update w - h u or a dot product needs.
+__device__ __forceinline__ dw dw_fma(dw a, dw b, dw c) {
+  const float ph = __fmul_rn(a.hi, b.hi);
+  float pl = __fmaf_rn(a.hi, b.hi, -ph);
+  pl = __fmaf_rn(a.hi, b.lo, pl);
+  pl = __fmaf_rn(a.lo, b.hi, pl);
+  float sh, sl, zh, zl;
+  two_sum(ph, c.hi, sh, sl);
+  sl = __fadd_rn(sl, __fadd_rn(pl, c.lo));
+  fast_two_sum(sh, sl, zh, zl);
+  return dw::make(zh, zl);
+}
+
 __device__ __forceinline__ dw operator-(dw x) { return dw::make(-x.hi, -x.lo); }
 __device__ __forceinline__ dw operator+(dw x, dw y) { return dw_add(x, y); }
 __device__ __forceinline__ dw operator-(dw x, dw y) { return dw_add(x, -y); }

@@ -253,6 +253,11 @@ __device__ __forceinline__ dw ldg_val(const dw* p) {
   return dw::make(t.x, t.y);
 }
 
+// a * b + c in the vector arithmetic (contracted to one FMA for FP64 and FP32 vectors)
+__device__ __forceinline__ double madd(double a, double b, double c) { return a * b + c; }
+__device__ __forceinline__ float madd(float a, float b, float c) { return a * b + c; }
+__device__ __forceinline__ dw madd(dw a, dw b, dw c) { return dw_fma(a, b, c); }
+
 // Per-thread accumulation of inner products (a += x * y), block-level sums (a += b) and the FP64
 // value of an accumulator, for every vector element type.
 __device__ __forceinline__ void dot_add(double& a, double x, double y) { a = fma(x, y, a); }
@@ -261,7 +266,7 @@ __device__ __forceinline__ void dot_sum(double& a, double b) { a += b; }
 __device__ __forceinline__ void dot_sum(float& a, float b) { a += b; }
 __device__ __forceinline__ double dot_val(double a) { return a; }
 __device__ __forceinline__ double dot_val(float a) { return (double)a; }
-__device__ __forceinline__ void dot_add(dw& a, dw x, dw y) { a = dw_add(a, dw_mul(x, y)); }
+__device__ __forceinline__ void dot_add(dw& a, dw x, dw y) { a = dw_fma(x, y, a); }
 __device__ __forceinline__ void dot_sum(dw& a, dw b) { a = dw_add(a, b); }
 __device__ __forceinline__ double dot_val(dw a) { return to_double(a); }
 
@@ -682,7 +687,7 @@ struct Engine {
       const V* usrc[PM];
 #pragma unroll
       for (int k = 0; k < PM; ++k) {
-        cA[k] = (k < p) ? ccoefA(k) : (A)0;
+        cA[k] = (k < p) ? -ccoefA(k) : (A)0;  // negated
         sg[k] = (k < p) ? (A)sig(j0 + k) : (A)0;
         usrc[k] = uslot(j0 + k);
       }
@@ -771,7 +776,7 @@ struct Engine {
               if (ci[e][qq] >= 0 && ct < (uint64_t)rows) {
 #pragma unroll
                 for (int k = 0; k < PM; ++k)
-                  if (k < p) wk[k][e] += cv[e][qq] * tl[k * T + ct];
+                  if (k < p) wk[k][e] = madd(cv[e][qq], tl[k * T + ct], wk[k][e]);
               }
             }
 #pragma unroll
@@ -786,7 +791,7 @@ struct Engine {
               for (int qq = 0; qq < QH; ++qq)
 #pragma unroll
                 for (int k = 0; k < PM; ++k)
-                  if (k < p) wk[k][e] += cv[e][h + qq] * gv[qq][k];
+                  if (k < p) wk[k][e] = madd(cv[e][h + qq], gv[qq][k], wk[k][e]);
             }
           }
         }
@@ -804,7 +809,7 @@ struct Engine {
             if (k < p) {
               sld<GG>(sp + (PM + k) * T, x);
 #pragma unroll
-              for (int e = 0; e < GG; ++e) wp[e] -= cA[k] * x[e];
+              for (int e = 0; e < GG; ++e) wp[e] = madd(cA[k], x[e], wp[e]);
             }
         }
 #pragma unroll
@@ -859,16 +864,16 @@ struct Engine {
     A cB[PM], cA[PM], cgb[NBMAX];
 #pragma unroll
     for (int k = 0; k < PM; ++k) {
-      cB[k] = (k < p) ? ccoefB(k) : (A)0;
-      cA[k] = (k < p - 1) ? ccoefA(k) : (A)0;
+      cB[k] = (k < p) ? -ccoefB(k) : (A)0;  // negated: the updates are w + (-h) u
+      cA[k] = (k < p - 1) ? -ccoefA(k) : (A)0;
     }
-    const A cA_last = ccoefA(p - 1);  // multiplies u_j
+    const A cA_last = -ccoefA(p - 1);  // multiplies u_j (negated)
     bool gB[NBMAX], gA[NBMAX];
 #pragma unroll
     for (int g = 0; g < NBMAX; ++g) {
       gB[g] = EXTRA && ghost_active(g, j);
       gA[g] = EXTRA && ghost_active(g, j + 1);
-      cgb[g] = gB[g] ? ccgB(g) : (A)0;
+      cgb[g] = gB[g] ? -ccgB(g) : (A)0;
     }
     V* wout = uslot(j + p);
     const V* wcur = wslot(t);
@@ -912,7 +917,7 @@ struct Engine {
         if (k < p) {
           sld<GG>(sp + (SUB + k) * T, x);
 #pragma unroll
-          for (int e = 0; e < GG; ++e) w[e] -= cB[k] * x[e];
+          for (int e = 0; e < GG; ++e) w[e] = madd(cB[k], x[e], w[e]);
         }
       if constexpr (EXTRA) {
 #pragma unroll
@@ -920,7 +925,7 @@ struct Engine {
           if (gB[g]) {
             vld<GG>(ghostv(g) + r, x);
 #pragma unroll
-            for (int e = 0; e < GG; ++e) w[e] -= cgb[g] * x[e];
+            for (int e = 0; e < GG; ++e) w[e] = madd(cgb[g], x[e], w[e]);
           }
       }
       vst<GG>(wout + r, w);
@@ -960,11 +965,11 @@ struct Engine {
           if (k < p - 1 && k >= ka) {
             sld<GG>(sp + (SUA + k) * T, x);
 #pragma unroll
-            for (int e = 0; e < GG; ++e) w1[e] -= cA[k] * x[e];
+            for (int e = 0; e < GG; ++e) w1[e] = madd(cA[k], x[e], w1[e]);
           }
         sld<GG>(sp + SUB * T, x);
 #pragma unroll
-        for (int e = 0; e < GG; ++e) w1[e] -= cA_last * x[e];
+        for (int e = 0; e < GG; ++e) w1[e] = madd(cA_last, x[e], w1[e]);
 #pragma unroll
         for (int k = 0; k < PM - 1; ++k)
           if (k < p - 1) {
@@ -1298,7 +1303,7 @@ struct Engine {
             for (int q = 0; q < 2 * PM; ++q) {
               const A cb = cdirB(l, q);
 #pragma unroll
-              for (int e = 0; e < GG; ++e) mw[2 * PM + l][e] += cb * mw[l + q][e];
+              for (int e = 0; e < GG; ++e) mw[2 * PM + l][e] = madd(cb, mw[l + q][e], mw[2 * PM + l][e]);
             }
             vst<GG>(mout[l] + r, mw[2 * PM + l]);
           } else {
@@ -1307,6 +1312,21 @@ struct Engine {
           }
         }
         // iterate rows r .. r+GG-1 (row-major, p per row)
+        if constexpr (std::is_same<V, dw>::value) {  // element by element (no row-block array)
+          const V* xsrc = xst ? tl + SX * T + (size_t)o * p : a.X + r * p;
+          V* xr = a.X + r * (int64_t)p;
+#pragma unroll
+          for (int e = 0; e < GG; ++e)
+#pragma unroll
+            for (int c = 0; c < PM; ++c)
+              if (c < p) {
+                A s = xsrc[e * p + c];
+#pragma unroll
+                for (int l = 0; l < PM; ++l)
+                  if (l < L) s = madd(mw[2 * PM + l][e], cZ(l, c), s);
+                xr[e * p + c] = s;
+              }
+        } else {
         const V* xsrc = xst ? tl + SX * T + (size_t)o * p : a.X + r * p;
         V* xr = a.X + r * (int64_t)p;
         A xs[GG][PM];
@@ -1323,7 +1343,7 @@ struct Engine {
               A s = xs[e][c];
 #pragma unroll
               for (int l = 0; l < PM; ++l)
-                if (l < L) s += mw[2 * PM + l][e] * cZ(l, c);
+                if (l < L) s = madd(mw[2 * PM + l][e], cZ(l, c), s);
               xs[e][c] = s;
             }
         if (xvec) {  // p == PM: 16-byte stores, flat index f = e * PM + c
@@ -1350,6 +1370,7 @@ struct Engine {
             for (int c = 0; c < PM; ++c)
               if (c < p) xr[e * p + c] = xs[e][c];
         }
+        }
         if (update_bench) {
 #pragma unroll
           for (int b = 0; b < NBMAX; ++b)
@@ -1364,7 +1385,7 @@ struct Engine {
                 if (l < p) {
                   const A cc = cbc(b0 + b, cyc & 1, l);
 #pragma unroll
-                  for (int e = 0; e < GG; ++e) v[e] -= cc * uv[l][e];
+                  for (int e = 0; e < GG; ++e) v[e] = madd(-cc, uv[l][e], v[e]);
                 }
               vst<GG>(bench(b0 + b) + r, v);
             }
