@@ -61,6 +61,19 @@ def workload(N: int):
     return A, B
 
 
+def pass_bytes(n: int, nnz: int, p: int, nb: int, s: int, sx: int):
+    """Algorithmic bytes per band iteration of each streaming pass as this design moves them, each
+    vector element read or written once per pass (element size s, iterate element size sx):
+    fused window pass (w', p window vectors, W_{t+1}, p-1 known vectors, nb bench in; w, W_{t+1} out;
+    the last iteration of a cycle has no A step), block product once per cycle (CSR, 2p vectors in,
+    p out) and the direction/iterate pass once per cycle (2p old directions, p Lanczos vectors, the
+    iterate and nb bench vectors in; p directions, the iterate and nb bench vectors out)."""
+    ba = ((p - 1) * (2 * p + 3 + nb) + (p + 2 + nb)) / p * n * s
+    sp = (4 * (n + 1) + nnz * (4 + s) + 3 * p * n * s) / p
+    dr = (4 * p * n * s + 2 * n * p * sx + 2 * nb * n * s) / p
+    return {"fused": ba, "block_product": sp, "directions": dr}
+
+
 def algorithmic(n: int, nnz: int, p: int, nb: int, s: int):
     """Algorithmic FLOPs and bytes of one band iteration ('Measurement').
 
@@ -71,6 +84,28 @@ def algorithmic(n: int, nnz: int, p: int, nb: int, s: int):
     flops = 2.0 * nnz + (6 * p + 4) * n + 4 * nb * n + (6 * p + 1) * n
     bytes_ = (nnz * (s + 4) + 4 * (n + 1)) / p + 2 * n * s + (2 * p + 3) * n * s + 6 * n * s + 3.0 * nb / p * n * s
     return flops, bytes_
+
+
+# DRAM bytes per band iteration of bminres_solve_kernel<double,8> on this workload, from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum of a 160-iteration launch, less its set-up, per
+# iteration); None when the kernel has changed since the counters were taken
+TRAFFIC_PER_ITER_F64 = 568.7e6
+
+
+def passes_report(info, n, nnz, p, s, sx, hbm_peak):
+    """Per-pass time per band iteration (block 0's device timeline) and algorithmic HBM rate."""
+    it = max(info["iters"], 1)
+    t = {"fused": (info["stream_ms"] - info["spmm_ms"] - info["dir_ms"]) / it,
+         "block_product": info["spmm_ms"] / it, "directions": info["dir_ms"] / it}
+    b = pass_bytes(n, nnz, p, 2, s, sx)
+    out = {}
+    for k in t:
+        gbs = b[k] / (t[k] * 1e-3) / 1e9 if t[k] > 0 else None
+        out[k] = {"us_per_iter": 1e3 * t[k], "bytes_per_iter": b[k], "gbs": gbs,
+                  "hbm_frac": gbs / hbm_peak if gbs else None}
+    out["reduce_us_per_iter"] = 1e3 * info["reduce_ms"] / it
+    out["scalar_us_per_iter"] = 1e3 * info["scalar_ms"] / it
+    return out
 
 
 class ClockSampler:
@@ -229,9 +264,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream().cuda_stream
     hbm_peak, peak_src = peaks()
     results = {}
-    modes = ["fp64", "mixed"] if args.mode == "both" else [args.mode]
+    modes = ["fp64", "mixed_dw"] if args.mode == "both" else args.mode.split(",")
     for mode in modes:
-        with Solver(A, precision=mode, bench=4) as s:
+        kw = {"tol_inner": args.tol_inner} if mode != "fp64" else {}
+        with Solver(A, precision=mode, bench=4, **kw) as s:
             for _ in range(args.warmup):  # short solves: module load, allocation, clocks
                 one_solve(s, Bh, Xh, args.warmup_maxit, stream)
             barrier(td)
@@ -251,7 +287,7 @@ def run_ours(args):
     value = max_over_ranks(td, statistics.median(dev))
     e2e = max_over_ranks(td, statistics.median(walls))
     info = steps[-1][0]
-    s_elem = 8 if head == "fp64" else 4
+    s_elem = 4 if head == "mixed" else 8
     fl, by = algorithmic(n, A.nnz, p, 2, s_elem)
     iters = info["iters"]
     kern_s = info["kernel_ms"] * 1e-3
@@ -261,13 +297,17 @@ def run_ours(args):
                 "traffic": None, "kernel": "bminres_solve_kernel<double,8>"}
     else:
         roof = {"bound": "hbm", "achieved": by * iters / kern_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                "peak_source": peak_src, "traffic": None, "kernel": "bminres_solve_kernel<float,8>"}
+                "peak_source": peak_src, "traffic": None,
+                "kernel": "bminres_solve_kernel<float,8>" if head == "mixed" else "bminres_solve_kernel<dw,8>"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["hbm_gbs"] = by * iters / kern_s / 1e9
     roof["hbm_frac"] = roof["hbm_gbs"] / hbm_peak
+    if head == "fp64" and TRAFFIC_PER_ITER_F64:
+        roof["traffic"] = TRAFFIC_PER_ITER_F64 * iters
+    roof["passes"] = passes_report(info, n, A.nnz, p, s_elem, 8 if head == "fp64" else s_elem, hbm_peak)
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if head == "fp64" else "f32+f64", "data": "synthetic",
+            "dtype": {"fp64": "f64", "mixed": "f32+f64", "mixed_dw": "f32x2+f64"}[head], "data": "synthetic",
             "config": {"workload": f"3D 7-point Laplacian {args.grid}^3 shifted at 10% of the spectrum, p=8 with two "
                                    "dependent columns, tol 1e-10", "mode": head, "n": n, "nnz": A.nnz, "p": p,
                        "band_iterations": iters, "cycles": info["cycles"], "setup_deflations": info["setup_deflations"],
@@ -276,7 +316,8 @@ def run_ours(args):
                        "l2": "inputs and per-solve traffic larger than L2 (no flush needed)",
                        "warmup": f"{args.warmup} solves capped at {args.warmup_maxit} band iterations",
                        "parallelism": f"{ws} independent replica(s)", "timeline_ms": {
-                           k: info[k] for k in ("kernel_ms", "stream_ms", "reduce_ms", "scalar_ms", "qr_ms")}},
+                           k: info[k] for k in ("kernel_ms", "stream_ms", "spmm_ms", "dir_ms", "reduce_ms", "scalar_ms",
+                                                "qr_ms")}},
             "roofline": roof,
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 2 * n * p * 8, "d2h_bytes_per_step": n * p * 8},
             "gpu_launches": info["launches"], "clocks": clocks}
@@ -284,12 +325,14 @@ def run_ours(args):
         if mode == head:
             continue
         inf = st[-1][0]
-        flm, bym = algorithmic(n, A.nnz, p, 2, 4)
+        se = 4 if mode == "mixed" else 8
+        flm, bym = algorithmic(n, A.nnz, p, 2, se)
         line[mode] = {"value": statistics.median([x[0]["device_ms"] * 1e-3 for x in st]), "unit": "s",
                       "band_iterations": inf["iters"], "outer": inf["outer"], "relres_true_max": inf["relres_true_max"],
                       "status": inf["status_name"], "e2e_s": statistics.median([x[2] for x in st]),
                       "hbm_gbs": bym * inf["iters"] / (inf["kernel_ms"] * 1e-3) / 1e9,
-                      "us_per_band_iteration": 1e3 * inf["kernel_ms"] / max(inf["iters"], 1)}
+                      "us_per_band_iteration": 1e3 * inf["kernel_ms"] / max(inf["iters"], 1),
+                      "tol_inner": args.tol_inner, "passes": passes_report(inf, n, A.nnz, p, se, se, hbm_peak)}
         line[mode]["hbm_frac"] = line[mode]["hbm_gbs"] / hbm_peak
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(A, B, iters, args.cpu_sample_iters)
@@ -324,7 +367,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--warmup-maxit", type=int, default=2000)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["fp64", "mixed", "both"], default="fp64")
+    ap.add_argument("--mode", default="fp64",
+                    help="fp64 (default), mixed, mixed_dw, a comma-separated list, or both (= fp64,mixed_dw)")
+    ap.add_argument("--tol-inner", type=float, default=1e-6, help="inner tolerance of the mixed forms")
     ap.add_argument("--grid", type=int, default=128)
     ap.add_argument("--cpu-sample-iters", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
