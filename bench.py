@@ -291,7 +291,7 @@ def run_ours(args):
     fl, by = algorithmic(n, A.nnz, p, 2, s_elem)
     iters = info["iters"]
     kern_s = info["kernel_ms"] * 1e-3
-    if head == "fp64":
+    if head in ("fp64", "fp64_refined"):
         roof = {"bound": "alu", "achieved": fl * iters / kern_s / 1e9, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                 "peak_source": "nominal FP64 of GB300 (1.25 TFLOP/s; 1.19 measured by an FMA probe)",
                 "traffic": None, "kernel": "bminres_solve_kernel<double,8>"}
@@ -307,7 +307,8 @@ def run_ours(args):
     roof["passes"] = passes_report(info, n, A.nnz, p, s_elem, 8 if head == "fp64" else s_elem, hbm_peak)
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "mixed": "f32+f64", "mixed_dw": "f32x2+f64"}[head], "data": "synthetic",
+            "dtype": {"fp64": "f64", "fp64_refined": "f64", "mixed": "f32+f64", "mixed_dw": "f32x2+f64"}[head],
+            "data": "synthetic",
             "config": {"workload": f"3D 7-point Laplacian {args.grid}^3 shifted at 10% of the spectrum, p=8 with two "
                                    "dependent columns, tol 1e-10", "mode": head, "n": n, "nnz": A.nnz, "p": p,
                        "band_iterations": iters, "cycles": info["cycles"], "setup_deflations": info["setup_deflations"],
@@ -368,7 +369,7 @@ def main():
     ap.add_argument("--warmup-maxit", type=int, default=2000)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", default="fp64",
-                    help="fp64 (default), mixed, mixed_dw, a comma-separated list, or both (= fp64,mixed_dw)")
+                    help="fp64 (default), fp64_refined, mixed, mixed_dw, a comma-separated list, or both (= fp64,mixed_dw)")
     ap.add_argument("--tol-inner", type=float, default=1e-6, help="inner tolerance of the mixed forms")
     ap.add_argument("--grid", type=int, default=128)
     ap.add_argument("--cpu-sample-iters", type=int, default=24)

@@ -42,7 +42,7 @@ typedef enum {
   BMINRES_ERR_TIMEOUT = -7         /* a device-side wait hit its time limit; results invalid */
 } bminres_status;
 
-typedef enum { BMINRES_FP64 = 0, BMINRES_MIXED = 1, BMINRES_MIXED_DW = 2 } bminres_precision;
+typedef enum { BMINRES_FP64 = 0, BMINRES_MIXED = 1, BMINRES_MIXED_DW = 2, BMINRES_FP64_REFINED = 3 } bminres_precision;
 
 typedef struct {
   int precision;     /* BMINRES_FP64 (default); BMINRES_MIXED: FP32 Lanczos vectors, block
@@ -50,7 +50,9 @@ typedef struct {
                         the residual B - A X, coefficients, band QR and dependence test in FP64;
                         BMINRES_MIXED_DW: the same loop with double-word vectors (pairs of FP32
                         values, about 48 significant bits, arithmetic on the FP32 units), p <= 16
-                        (larger p: BMINRES_ERR_INVALID).  Neither mixed form is in the paper */
+                        (larger p: BMINRES_ERR_INVALID); BMINRES_FP64_REFINED: the same loop with
+                        FP64 inner solves (restarts until the FP64 true residual meets tol).
+                        None of the refined forms is in the paper */
   double gamma;      /* dependence tolerance, relative: a new vector is dependent when its norm
                         after orthogonalisation is <= gamma * ||A u_j|| (Sec. 5).  Default 1e-8;
                         FP32 inner solves (MIXED) use max(gamma, 1e-5) */
@@ -59,8 +61,8 @@ typedef struct {
   int ghost;         /* 1: keep a removed vector and orthogonalise against it for the next 2p
                         iterations (end of Sec. 5.1).  Its coefficients are not part of H, so the
                         recursive residual can then drift from the true one.  Default 0 */
-  double tol_inner;  /* MIXED, MIXED_DW: relative tolerance of each inner solve.  Default 1e-5 */
-  int max_outer;     /* MIXED, MIXED_DW: maximum refinement steps.  Default 20 */
+  double tol_inner;  /* refined forms: relative tolerance of each inner solve.  Default 1e-5 */
+  int max_outer;     /* refined forms: maximum refinement steps.  Default 20 */
   int max_blocks;    /* upper bound on the persistent kernel's grid (0 = one wave of the GPU) */
 } bminres_opts;
 

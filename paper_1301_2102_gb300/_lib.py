@@ -17,7 +17,7 @@ STATUS = {0: "BMINRES_OK", 1: "BMINRES_NOT_CONVERGED", -1: "BMINRES_ERR_INVALID"
           -3: "BMINRES_ERR_OOM", -4: "BMINRES_ERR_BREAKDOWN", -5: "BMINRES_ERR_BENCH_EXHAUSTED",
           -6: "BMINRES_ERR_NONFINITE", -7: "BMINRES_ERR_TIMEOUT"}
 OK, NOT_CONVERGED = 0, 1
-FP64, MIXED, MIXED_DW = 0, 1, 2
+FP64, MIXED, MIXED_DW, FP64_REFINED = 0, 1, 2, 3
 
 
 class Opts(ctypes.Structure):

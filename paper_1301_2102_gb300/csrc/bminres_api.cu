@@ -158,9 +158,14 @@ void free_ws(bmr::Workspace& w) {
   w = bmr::Workspace();
 }
 
-// vector precision of the solves of a handle: 0 = FP64, 1 = FP32, 2 = double-word
+// vector precision of the solves of a handle: 0 = FP64, 1 = FP32, 2 = double-word, 3 = FP64 refined
 int prec_of(bminres_handle h) {
-  return h->opts.precision == BMINRES_MIXED ? 1 : (h->opts.precision == BMINRES_MIXED_DW ? 2 : 0);
+  switch (h->opts.precision) {
+    case BMINRES_MIXED: return 1;
+    case BMINRES_MIXED_DW: return 2;
+    case BMINRES_FP64_REFINED: return 3;
+  }
+  return 0;
 }
 
 // (Re)allocate the workspace for block size p and vector precision prec (see prec_of).
@@ -410,8 +415,10 @@ bminres_status solve_device(bminres_handle h, int p, const double* B, double* X,
     st = map_kernel_status(r.status);
   } else if (prec == 1) {
     st = refine<float>(h, p, B, X, tol, maxit, s, f0, inf);
-  } else {
+  } else if (prec == 2) {
     st = refine<bmr::dw>(h, p, B, X, tol, maxit, s, f0, inf);
+  } else {
+    st = refine<double>(h, p, B, X, tol, maxit, s, f0, inf);
   }
   // FP64 true residual of the result
   st = (st == BMINRES_OK || st == BMINRES_NOT_CONVERGED) ? st : st;
@@ -480,7 +487,7 @@ bminres_status bminres_create(bminres_handle* out, int64_t n, int64_t nnz, const
   bminres_opts o;
   bminres_default_opts(&o);
   if (opts) o = *opts;
-  if (o.bench < 0 || o.bench > bmr::NBMAX || !(o.gamma >= 0.0) || (o.precision != BMINRES_FP64 && o.precision != BMINRES_MIXED && o.precision != BMINRES_MIXED_DW))
+  if (o.bench < 0 || o.bench > bmr::NBMAX || !(o.gamma >= 0.0) || (o.precision < BMINRES_FP64 || o.precision > BMINRES_FP64_REFINED))
     return BMINRES_ERR_INVALID;
   if (o.max_outer <= 0) o.max_outer = 20;
   if (!(o.tol_inner > 0.0)) o.tol_inner = 1e-5;

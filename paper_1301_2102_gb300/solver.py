@@ -51,7 +51,7 @@ class Solver:
         colidx = np.ascontiguousarray(colidx, dtype=np.int32)
         vals = np.ascontiguousarray(vals, dtype=np.float64)
         o = _lib.default_opts()
-        o.precision = {"fp64": _lib.FP64, "mixed": _lib.MIXED, "mixed_dw": _lib.MIXED_DW}[precision]
+        o.precision = {"fp64": _lib.FP64, "mixed": _lib.MIXED, "mixed_dw": _lib.MIXED_DW, "fp64_refined": _lib.FP64_REFINED}[precision]
         o.gamma = gamma
         o.bench = bench
         o.seed = seed & ((1 << 64) - 1)

@@ -186,6 +186,18 @@ def test_double_word_refinement_reaches_tol(torch_cuda, oracle_mod, workloads):
     assert np.linalg.norm(X - ref.X) / np.linalg.norm(ref.X) < 1e-7
 
 
+def test_fp64_refined_reaches_true_tol(torch_cuda, oracle_mod, workloads):
+    """FP64 inner solves inside the refinement loop: the FP64 true residual meets tol (one restart
+    at most here) and the result agrees with the oracle."""
+    A = workloads.laplacian(16, 3, workloads.shift_at_fraction(16, 3, 0.1))
+    B = workloads.randn_rhs(A.n, 4, 3)
+    ref = oracle_mod.bminres(A, B, tol=1e-10, maxit=40000)
+    X, info, rel = _solve(torch_cuda, A, B, maxit=200000, precision="fp64_refined", tol_inner=1e-6)
+    assert info["status"] == 0 and 1 <= info["outer"] <= 3, info
+    assert rel.max() < 1e-10
+    assert np.linalg.norm(X - ref.X) / np.linalg.norm(ref.X) < 1e-7
+
+
 def test_double_word_rejects_p_above_16(torch_cuda, workloads):
     from paper_1301_2102_gb300 import Solver
     from paper_1301_2102_gb300._lib import BminresError

@@ -427,3 +427,55 @@ def test_removed_vector_retention_breaks_the_residual_recursion(oracle_mod, work
     assert keep.status == 0 and drop.status == 0  # both stopping tests are met
     assert oracle_mod.relres(A, B, drop.X).max() < 2e-10
     assert oracle_mod.relres(A, B, keep.X).max() > 1e-6
+
+
+# ---------------------------------------------------------------------------------------------
+# P13: the adjoint of the block solve (spec extension, not in the paper)
+# ---------------------------------------------------------------------------------------------
+
+def _symmetric_pairs(A):
+    """(k, k') index pairs of the stored entries a_rc and a_cr, r <= c."""
+    pos = {}
+    for r in range(A.n):
+        for k in range(A.rowptr[r], A.rowptr[r + 1]):
+            pos[(r, int(A.colidx[k]))] = k
+    return [(k, pos[(c, r)]) for (r, c), k in pos.items() if r <= c]
+
+
+def adjoint_from_oracle(oracle_mod, A, X, G):
+    """dL/dB = A^{-1} G (one more oracle block solve, A symmetric) and dL/dA_k = -dB[r_k] . X[c_k]
+    on the stored pattern, for L with dL/dX = G."""
+    dB = oracle_mod.bminres(A, G, tol=1e-14, maxit=20 * A.n).X
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    dA = -np.einsum("kc,kc->k", dB[rows], X[A.colidx])
+    return dB, dA
+
+
+def test_P13_adjoint_matches_finite_differences(oracle_mod, workloads):
+    """The backward formulas built on oracle solves against central finite differences of a dense
+    LU solve (B entries and symmetric pairs of A, L = sum(W * X))."""
+    A = workloads.saddle_point(6, 12, 3, seed=4)
+    n, p = A.n, 3
+    rng = np.random.default_rng(13)
+    B = rng.standard_normal((n, p))
+    W = rng.standard_normal((n, p))
+    X = oracle_mod.bminres(A, B, tol=1e-14, maxit=20 * n).X
+    dB, dA = adjoint_from_oracle(oracle_mod, A, X, W)
+    D = A.to_dense()
+    L = lambda M, Bm: float(np.sum(W * np.linalg.solve(M, Bm)))
+    h = 1e-6
+    for (i, c) in [(0, 0), (n // 2, 1), (n - 1, 2), (7, 0)]:
+        Bp, Bm = B.copy(), B.copy()
+        Bp[i, c] += h
+        Bm[i, c] -= h
+        fd = (L(D, Bp) - L(D, Bm)) / (2 * h)
+        assert abs(fd - dB[i, c]) <= 1e-6 * max(1.0, abs(fd))
+    pairs = _symmetric_pairs(A)
+    for k, kt in [pairs[i] for i in (0, len(pairs) // 3, len(pairs) // 2, len(pairs) - 1)]:
+        r = int(np.searchsorted(A.rowptr, k, side="right") - 1)
+        cc = int(A.colidx[k])
+        E = np.zeros_like(D)
+        E[r, cc] = E[cc, r] = 1.0
+        fd = (L(D + h * E, B) - L(D - h * E, B)) / (2 * h)
+        an = dA[k] + (dA[kt] if kt != k else 0.0)
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd))
