@@ -11,6 +11,10 @@ with B and X in pinned host memory: `value` is the CUDA-event time of the device
 is known), `e2e` is the host wall time of the whole call (host->device copy of B and X0, solve,
 device->host copy of X).  The inputs (134 MB per block) and the per-solve traffic (GBs) exceed L2.
 
+`--mode` adds the refined forms (fp64_refined, mixed_dw, mixed: FP64 iterative refinement around
+FP64, double-word or FP32 inner solves, each to an FP64 true residual below tol) as extra objects of
+the same line; the first mode listed is the headline.
+
 `--impl reference` times the CPU oracle (plain C, FP64, one core) on the same workload: set-up plus
 a bounded number of band iterations, scaled to a full solve.  Under torchrun every rank runs its own
 replica of the solve (the method does not shard across GPUs here); rank 0 prints the JSON line.

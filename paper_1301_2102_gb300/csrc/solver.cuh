@@ -27,8 +27,12 @@
 //     them to the new column is one small matrix-vector product; the p rotations of the new column
 //     come from prefix norms in closed form.
 //   * Lanczos vectors are stored unnormalised with a per-slot scale sigma_i (u_i = sigma_i raw_i).
+//   * The streaming passes read their vectors through shared memory: tiles of rows are copied by
+//     bulk asynchronous copies (cp.async.bulk, completion on an mbarrier) into two staging buffers,
+//     two tiles ahead of the threads that compute on them (Engine::tiles); results go straight to
+//     global memory.
 //
-// Data layout (all vectors have stride `ld` elements, V = double or float):
+// Data layout (all vectors have stride `ld` elements, V = double, float or dw (double-word)):
 //   U     2p ring slots, u_i in slot i mod 2p        (band Lanczos FIFO, Sec. 7)
 //   W     p slots: block product, overwritten in place by the partly orthogonalised w'
 //   M     2p ring slots, m_i in slot i mod 2p        (search-direction FIFO, Sec. 7)
