@@ -122,6 +122,14 @@ def laplacian_null_modes_2d(N: int, sigma: float) -> np.ndarray:
     return np.stack(modes, axis=1)
 
 
+def paper_e1_operator(N: int = 200) -> CSR:
+    """The operator of the paper's first experiment (Sec. 8): A = -L - 200 I with L the 2D 5-point
+    Laplacian on an N x N grid, h = 1/(N - 1), here scaled by h^2 (the unscaled stencil minus
+    200 h^2 I), which changes no relative residual."""
+    h = 1.0 / (N - 1)
+    return laplacian(N, 2, 200.0 * h * h)
+
+
 def randn_rhs(n: int, p: int, seed: int = 0) -> np.ndarray:
     """``(n, p)`` row-major float64 matrix of i.i.d. N(0,1) entries."""
     rng = np.random.default_rng(seed)

@@ -7,6 +7,7 @@ import socket
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -75,3 +76,13 @@ def test_reference_arm_under_torchrun_prints_one_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_paper_e1_operator():
+    from paper_1301_2102_gb300 import workloads
+
+    A = workloads.paper_e1_operator(20)
+    h = 1.0 / 19
+    D = A.to_dense()
+    assert A.n == 400 and np.allclose(np.diag(D), 4.0 - 200.0 * h * h)
+    assert np.allclose(D, D.T) and set(np.unique(D[D != np.diag(D)[0]]).tolist()) <= {-1.0, 0.0}
