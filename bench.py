@@ -90,10 +90,11 @@ def algorithmic(n: int, nnz: int, p: int, nb: int, s: int):
     return flops, bytes_
 
 
-# DRAM bytes per band iteration of bminres_solve_kernel<double,8> on this workload, from ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum of a 160-iteration launch, less its set-up, per
-# iteration); None when the kernel has changed since the counters were taken
-TRAFFIC_PER_ITER_F64 = 568.7e6
+# DRAM bytes of bminres_solve_kernel<double,8> on this workload, from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum of launches of 160 and 320 band iterations: 90.995 GB and 180.260 GB, i.e.
+# 557.9 MB per band iteration plus 1.73 GB of set-up); None when the kernel has changed since
+TRAFFIC_PER_ITER_F64 = 557.9e6
+TRAFFIC_SETUP_F64 = 1.73e9
 
 
 def passes_report(info, n, nnz, p, s, sx, hbm_peak):
@@ -307,7 +308,7 @@ def run_ours(args):
     roof["hbm_gbs"] = by * iters / kern_s / 1e9
     roof["hbm_frac"] = roof["hbm_gbs"] / hbm_peak
     if head == "fp64" and TRAFFIC_PER_ITER_F64:
-        roof["traffic"] = TRAFFIC_PER_ITER_F64 * iters
+        roof["traffic"] = TRAFFIC_SETUP_F64 + TRAFFIC_PER_ITER_F64 * iters
     roof["passes"] = passes_report(info, n, A.nnz, p, s_elem, 8 if head == "fp64" else s_elem, hbm_peak)
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
