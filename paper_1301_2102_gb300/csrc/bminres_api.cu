@@ -296,6 +296,16 @@ bminres_status persistent_solve(bminres_handle h, int p, V* Xout, double tol, in
   a.rho_hist = h->hist;
   a.hist_cap = h->hist_cap;
   a.barrier_limit_ns = BARRIER_LIMIT_NS;
+  // Fault injection for tests of the bounded waits (no GPU fault involved): with
+  // BMINRES_DEBUG_BARRIER_TIMEOUT_MS set, every grid barrier waits for one block more than the
+  // grid has and gives up after that many milliseconds, so the solve ends with BMINRES_ERR_TIMEOUT.
+  if (const char* e = getenv("BMINRES_DEBUG_BARRIER_TIMEOUT_MS")) {
+    const long ms = strtol(e, nullptr, 10);
+    if (ms > 0) {
+      a.barrier_limit_ns = (unsigned long long)ms * 1000000ull;
+      a.barrier_extra = 1;
+    }
+  }
   BMR_TRY(cudaEventRecord(h->evk0, s));
   BMR_TRY(launch_solve<V>(pm_for(p), a, w.grid, s));
   BMR_TRY(cudaEventRecord(h->evk1, s));

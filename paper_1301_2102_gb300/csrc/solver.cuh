@@ -73,6 +73,7 @@ struct SolveArgs {
   double* rho_hist;  // optional: [hist_cap][p] recursive residual norms
   int hist_cap;
   unsigned long long barrier_limit_ns;
+  unsigned barrier_extra;  // fault injection: arrivals a grid barrier waits for beyond the grid (0)
 };
 
 template <int PM>
@@ -499,7 +500,7 @@ struct Engine {
     for (int v = tid; v < nv; v += NT)
       part[(int64_t)v * nblocks + blockIdx.x] = (sh.d4[v][0] + sh.d4[v][1]) + (sh.d4[v][2] + sh.d4[v][3]);
     buf ^= 1;
-    if (!grid_barrier(a.ctl, nblocks, sh.bar_epoch, a.barrier_limit_ns)) return false;
+    if (!grid_barrier(a.ctl, nblocks + a.barrier_extra, sh.bar_epoch, a.barrier_limit_ns)) return false;
     for (int task = tid; task < nv * 32; task += NT) {
       int v = task >> 5, l = task & 31;
       const double* pv = part + (int64_t)v * nblocks;
