@@ -91,10 +91,10 @@ def algorithmic(n: int, nnz: int, p: int, nb: int, s: int):
 
 
 # DRAM bytes of bminres_solve_kernel<double,8> on this workload, from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum of launches of 160 and 320 band iterations: 90.995 GB and 180.260 GB, i.e.
-# 557.9 MB per band iteration plus 1.73 GB of set-up); None when the kernel has changed since
+# dram__bytes_write.sum of launches of 160 and 320 band iterations: 90.981 GB and 180.249 GB, i.e.
+# 557.9 MB per band iteration plus 1.71 GB of set-up); None when the kernel has changed since
 TRAFFIC_PER_ITER_F64 = 557.9e6
-TRAFFIC_SETUP_F64 = 1.73e9
+TRAFFIC_SETUP_F64 = 1.71e9
 
 
 def passes_report(info, n, nnz, p, s, sx, hbm_peak):
