@@ -68,15 +68,15 @@ typedef struct {
 
 typedef struct {
   int status;            /* same as the return value */
-  int iters;             /* band iterations (summed over inner solves in MIXED mode) */
+  int iters;             /* band iterations (summed over the inner solves of the refined forms) */
   int cycles;            /* block products A [u_j .. u_{j+p-1}] */
-  int outer;             /* refinement steps (MIXED); 1 in FP64 mode */
+  int outer;             /* refinement steps (MIXED, MIXED_DW, FP64_REFINED); 1 in FP64 mode */
   int deflations;        /* dependent vectors replaced during the iteration */
   int setup_deflations;  /* dependent columns of the initial block residual */
   int bench_used;        /* bench vectors consumed */
   int grid_blocks;       /* blocks of the persistent solve kernel */
   double relres_est_max; /* max_i of the recursive residual ||Shat(j+1:j+p, i)|| / ||f0_i||
-                            (Eq. (comp-resid)); in MIXED mode, of the last inner solve */
+                            (Eq. (comp-resid)); for the refined forms, of the last inner solve */
   double relres_true_max;/* max_i ||b_i - A x_i|| / ||b_i - A x0_i||, recomputed in FP64 */
   double device_ms;      /* device time from the first to the last kernel of the solve */
   double kernel_ms;      /* CUDA-event time of the persistent solve kernel launches (summed) */
@@ -109,10 +109,11 @@ bminres_status bminres_set_values(bminres_handle handle, const double* vals, bmi
 /* Solve A X = B by block MINRES (Algorithm 2).  B: n x p, X: n x p (in: X0, out: X).
  * Stops after the first band iteration j with max_i rho_i / ||f0_i|| < tol, where rho_i is the
  * recursive residual of column i (Eq. (comp-resid)) and f0 = B - A X0 (FP64 mode), or when the
- * FP64 true relative residual of every column is < tol (MIXED mode), or after maxit band
+ * FP64 true relative residual of every column is < tol (refined forms), or after maxit band
  * iterations (status NOT_CONVERGED, X = last iterate).  relres_true (host, length p, may be NULL)
  * receives ||b_i - A x_i|| / ||b_i - A x0_i|| computed in FP64 after the solve.  info may be
- * NULL.  p must satisfy 1 <= p <= 32 and p <= n; n = 0 or p = 0 returns BMINRES_OK at once. */
+ * NULL.  p must satisfy 1 <= p <= 32 (<= 16 for MIXED_DW) and p <= n; n = 0 or p = 0 returns
+ * BMINRES_OK at once. */
 bminres_status bminres_solve(bminres_handle handle, int p, const double* B, double* X, double tol,
                              int maxit, bminres_stream stream, double* relres_true, bminres_info* info);
 
@@ -126,8 +127,8 @@ bminres_status bminres_backward(bminres_handle handle, int p, const double* G, c
                                 bminres_stream stream, bminres_info* info);
 
 /* Record the recursive residual norms ||Shat(j+1:j+p, i)|| (Eq. (comp-resid)) of band iterations
- * j = 1 .. cap of the following solves (cap = 0 switches recording off).  In MIXED mode the
- * record is that of the last inner solve. */
+ * j = 1 .. cap of the following solves (cap = 0 switches recording off).  For the refined forms
+ * the record is that of the last inner solve. */
 bminres_status bminres_set_history(bminres_handle handle, int cap);
 
 /* Copy the record of the last solve to host memory: out[(j-1)*p + i] for j = 1 .. *count
