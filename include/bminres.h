@@ -10,7 +10,8 @@
  * Conventions for every entry point:
  *  - Dense blocks (B, X, G, dB) are row-major n x p arrays of double: entry (r, c) at [r*p + c].
  *  - A pointer argument may be host or device memory; host data is staged through buffers the
- *    handle owns.  The caller keeps ownership of every pointer it passes.
+ *    handle owns.  Device memory must belong to the current device (memory of another GPU is
+ *    rejected with BMINRES_ERR_INVALID).  The caller keeps ownership of every pointer it passes.
  *  - Work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default stream).  Entry
  *    points that fill an info struct or return a solve status synchronise that stream first.
  *  - Errors are returned as bminres_status codes; no exception crosses the ABI.  After any
@@ -33,6 +34,11 @@ typedef void* bminres_stream; /* cudaStream_t */
 typedef enum {
   BMINRES_OK = 0,                  /* converged: every column met the stopping test */
   BMINRES_NOT_CONVERGED = 1,       /* maxit reached; X holds the last iterate */
+  BMINRES_RESIDUAL_GAP = 2,        /* FP64 mode: the recursive residual met tol (the paper's stopping
+                                      test) but the FP64 true residual recomputed after the solve did
+                                      not (finite-precision residual gap, or a dropped dependent
+                                      direction); X holds the final iterate.  The refined forms
+                                      restart on this condition instead of returning it */
   BMINRES_ERR_INVALID = -1,        /* bad argument (sizes, CSR structure, null pointer) */
   BMINRES_ERR_CUDA = -2,           /* a CUDA runtime call failed, or no usable sm_103 device */
   BMINRES_ERR_OOM = -3,            /* device allocation failed */
@@ -110,7 +116,9 @@ bminres_status bminres_set_values(bminres_handle handle, const double* vals, bmi
  * Stops after the first band iteration j with max_i rho_i / ||f0_i|| < tol, where rho_i is the
  * recursive residual of column i (Eq. (comp-resid)) and f0 = B - A X0 (FP64 mode), or when the
  * FP64 true relative residual of every column is < tol (refined forms), or after maxit band
- * iterations (status NOT_CONVERGED, X = last iterate).  relres_true (host, length p, may be NULL)
+ * iterations (status NOT_CONVERGED, X = last iterate).  In FP64 mode the status is
+ * BMINRES_RESIDUAL_GAP instead of BMINRES_OK when the FP64 true residual of some column is above
+ * tol although the recursive one met it.  relres_true (host, length p, may be NULL)
  * receives ||b_i - A x_i|| / ||b_i - A x0_i|| computed in FP64 after the solve.  info may be
  * NULL.  p must satisfy 1 <= p <= 32 (<= 16 for MIXED_DW) and p <= n; n = 0 or p = 0 returns
  * BMINRES_OK at once. */
@@ -149,7 +157,7 @@ bminres_status bminres_spmm(bminres_handle handle, int p, const double* X, doubl
  * synchronisation of cudaMalloc / cudaFree.  The result is the same as bminres_create +
  * bminres_solve in FP64 mode with the default options (or *opts, whose precision must be FP64).
  *  - rowptr, colidx, vals (CSR of A, int32 indices, full symmetric pattern), B and X (row-major
- *    n x p; X in: X0, out: X) must be device pointers; the caller owns them.  The CSR is not
+ *    n x p; X in: X0, out: X) must be device pointers of the current device; the caller owns them.  The CSR is not
  *    validated beyond n >= 0 and 0 <= nnz < 2^31.
  *  - All workspace lives in one static device array of BMINRES_NOALLOC_SCRATCH_BYTES; the call
  *    fits when (6 p + 2 bench) * 8 * round_up(n, 64) bytes plus ~1 MiB do not exceed it (about
@@ -160,11 +168,20 @@ bminres_status bminres_spmm(bminres_handle handle, int p, const double* X, doubl
  *  - Every call shares the array and it keeps the last call's contents: calls that overlap on the
  *    GPU (other streams, other host threads) race and must not be issued.
  *  - relres_true (host, p doubles) and info may be NULL; info->device_ms is 0 (no event is
- *    created); info->timeline_ms carries the kernel's own device timer. */
+ *    created); info->timeline_ms carries the kernel's own device timer.  The status follows
+ *    bminres_solve in FP64 mode (BMINRES_RESIDUAL_GAP included). */
 bminres_status bminres_solve_noalloc(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colidx,
                                      const double* vals, int p, const double* B, double* X, double tol,
                                      int maxit, const bminres_opts* opts, bminres_stream stream,
                                      double* relres_true, bminres_info* info);
+
+/* Measurement helper, not a step of the method (the paper has no counterpart): FP64 fused
+ * multiply-add throughput of the current GPU, in GFLOP/s (2 flops per FMA), from one timed launch of
+ * independent FMA chains (8 blocks of 256 threads per SM, `iters` FMAs per chain and thread, 8
+ * chains per thread) after one warm-up launch, on `stream`.  It is the denominator of the arithmetic
+ * roofline against which the FP64 solve is reported.  ms (may be NULL) receives the timed launch's
+ * duration.  Allocates 8 bytes of device memory for the duration of the call. */
+bminres_status bminres_fp64_peak(int iters, bminres_stream stream, double* gflops, double* ms);
 
 /* Release the handle and everything it owns.  NULL is ignored. */
 void bminres_destroy(bminres_handle handle);

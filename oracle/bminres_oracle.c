@@ -45,6 +45,25 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Build variants of this one source (the arithmetic of the default build is plain FP64):
+ *   ORACLE_ACC   accumulator type of inner products, norms and the CSR matvec sums (default
+ *                double).  `long double` gives a second reference whose only difference is the
+ *                rounding of those sums; the tests use it to measure how much the iteration count
+ *                at which the tolerance is met depends on summation rounding.
+ *   ORACLE_OMP   (with -fopenmp) the vector loops and the matvec run on all host cores, the inner
+ *                products as fixed chunks summed in chunk order, so the result does not depend on
+ *                the thread count.  Used only to time the oracle on the host cores. */
+#ifndef ORACLE_ACC
+#define ORACLE_ACC double
+#endif
+typedef ORACLE_ACC acc_t;
+#if defined(ORACLE_OMP) && defined(_OPENMP)
+#define OMP_FOR _Pragma("omp parallel for schedule(static)")
+#define DOT_CHUNKS 256
+#else
+#define OMP_FOR
+#endif
+
 #define OR_OK 0
 #define OR_NOT_CONVERGED 1
 #define OR_ERR_INVALID -1
@@ -83,24 +102,44 @@ double oracle_bench_value(uint64_t seed, int64_t k, int64_t n, int64_t row) {
 
 /* ---------------------------------------------------------------------------------------- */
 static double dot(int64_t n, const double* x, const double* y) {
+#ifdef DOT_CHUNKS
+  double part[DOT_CHUNKS];
+  OMP_FOR
+  for (int c = 0; c < DOT_CHUNKS; ++c) {
+    acc_t s = 0.0;
+    for (int64_t r = n * c / DOT_CHUNKS; r < n * (c + 1) / DOT_CHUNKS; ++r) s += (acc_t)x[r] * y[r];
+    part[c] = (double)s;
+  }
   double s = 0.0;
-  for (int64_t r = 0; r < n; ++r) s += x[r] * y[r];
+  for (int c = 0; c < DOT_CHUNKS; ++c) s += part[c];
   return s;
+#else
+  acc_t s = 0.0;
+  for (int64_t r = 0; r < n; ++r) s += (acc_t)x[r] * y[r];
+  return (double)s;
+#endif
 }
 static void axpy(int64_t n, double a, const double* x, double* y) {
+  OMP_FOR
   for (int64_t r = 0; r < n; ++r) y[r] += a * x[r];
 }
 static double nrm2(int64_t n, const double* x) { return sqrt(dot(n, x, x)); }
 static void scal(int64_t n, double a, double* x) {
+  OMP_FOR
   for (int64_t r = 0; r < n; ++r) x[r] *= a;
+}
+static void vcopy(int64_t n, const double* x, double* y) {
+  OMP_FOR
+  for (int64_t r = 0; r < n; ++r) y[r] = x[r];
 }
 /* y = A x for CSR A */
 static void csr_matvec(int64_t n, const int32_t* rowptr, const int32_t* colidx, const double* vals,
                        const double* x, double* y) {
+  OMP_FOR
   for (int64_t r = 0; r < n; ++r) {
-    double s = 0.0;
-    for (int32_t k = rowptr[r]; k < rowptr[r + 1]; ++k) s += vals[k] * x[colidx[k]];
-    y[r] = s;
+    acc_t s = 0.0;
+    for (int32_t k = rowptr[r]; k < rowptr[r + 1]; ++k) s += (acc_t)vals[k] * x[colidx[k]];
+    y[r] = (double)s;
   }
 }
 
@@ -128,9 +167,9 @@ static void house_gen(int m, const double* x, double* v, double* tau, double* be
 /* y <- (I - tau v v^T) y over m entries with stride `ld` between consecutive entries */
 static void house_apply(int m, const double* v, double tau, double* y, int ld) {
   if (tau == 0.0) return;
-  double s = 0.0;
-  for (int t = 0; t < m; ++t) s += v[t] * y[(int64_t)t * ld];
-  s *= tau;
+  acc_t sa = 0.0;
+  for (int t = 0; t < m; ++t) sa += (acc_t)v[t] * y[(int64_t)t * ld];
+  double s = (double)sa * tau;
   for (int t = 0; t < m; ++t) y[(int64_t)t * ld] -= s * v[t];
 }
 
@@ -226,8 +265,10 @@ int oracle_bminres(int64_t n, const int32_t* rowptr, const int32_t* colidx, cons
     if (all_zero) { status = OR_OK; info->iters = 0; goto done; }
   }
   /* bench vectors, drawn before the iteration (Sec. 5.1) */
-  for (int k = 0; k < nb; ++k)
+  for (int k = 0; k < nb; ++k) {
+    OMP_FOR
     for (int64_t r = 0; r < n; ++r) Bench[(size_t)k * n + r] = oracle_bench_value(seed, k, n, r);
+  }
   int bench_next = 0, n_ghost = 0;
 
   /* ---- economy QR F0 = U_p S by modified Gram-Schmidt with one re-orthogonalisation pass,
@@ -235,7 +276,7 @@ int oracle_bminres(int64_t n, const int32_t* rowptr, const int32_t* colidx, cons
   int ucount = 0;
   for (int i = 0; i < p; ++i) {
     double* v = USLOT(i + 1);
-    memcpy(v, F0 + (size_t)i * n, sizeof(double) * n);
+    vcopy(n, F0 + (size_t)i * n, v);
     for (int pass = 0; pass < 2; ++pass)
       for (int k = 0; k < i; ++k) {
         double c = dot(n, USLOT(k + 1), v);
@@ -249,7 +290,7 @@ int oracle_bminres(int64_t n, const int32_t* rowptr, const int32_t* colidx, cons
       info->setup_deflations++;
       S[i * p + i] = 0.0;
       if (bench_next >= nb) { status = OR_ERR_BENCH_EXHAUSTED; goto done; }
-      memcpy(v, Bench + (size_t)bench_next * n, sizeof(double) * n);
+      vcopy(n, Bench + (size_t)bench_next * n, v);
       bench_next++;
       for (int pass = 0; pass < 2; ++pass)
         for (int k = 0; k < i; ++k) mgs_step(n, USLOT(k + 1), v);
@@ -280,7 +321,7 @@ int oracle_bminres(int64_t n, const int32_t* rowptr, const int32_t* colidx, cons
       for (int l = 0; l < p; ++l)
         csr_matvec(n, A.rowptr, A.colidx, A.vals, USLOT(j + l), Wb + (size_t)l * n);
     int l = (j - 1) % p;
-    memcpy(w, Wb + (size_t)l * n, sizeof(double) * n);
+    vcopy(n, Wb + (size_t)l * n, w);
     double normAu = nrm2(n, w);
     for (int t = 0; t < 3 * p + 1; ++t) col[t] = 0.0;
     /* col[t] holds row (j - 2p + t); H column rows j-p..j+p sit at t = p..3p */
@@ -312,7 +353,7 @@ int oracle_bminres(int64_t n, const int32_t* rowptr, const int32_t* colidx, cons
          * against u_{j-p+1}..u_{j+p-1} and the removed vectors active at j), normalised; for an
          * exact dependence w is rounding noise with O(1) components along the window */
         double* g = Ghost + (size_t)n_ghost * n;
-        memcpy(g, w, sizeof(double) * n);
+        vcopy(n, w, g);
         for (int i = (j - p + 1 > 1 ? j - p + 1 : 1); i <= j + p - 1; ++i) mgs_step(n, USLOT(i), g);
         for (int q = 0; q < n_ghost; ++q)
           if (ghost_born[q] < j && j <= ghost_born[q] + 2 * p) mgs_step(n, Ghost + (size_t)q * n, g);
@@ -323,7 +364,7 @@ int oracle_bminres(int64_t n, const int32_t* rowptr, const int32_t* colidx, cons
           n_ghost++;
         }
       }
-      memcpy(unew, Bench + (size_t)bench_next * n, sizeof(double) * n);
+      vcopy(n, Bench + (size_t)bench_next * n, unew);
       bench_next++;
       for (int i = (j - p + 1 > 1 ? j - p + 1 : 1); i <= j + p - 1; ++i) mgs_step(n, USLOT(i), unew);
       for (int g = 0; g < n_ghost; ++g)
@@ -334,7 +375,7 @@ int oracle_bminres(int64_t n, const int32_t* rowptr, const int32_t* colidx, cons
       scal(n, 1.0 / nr, unew);
       beta = 0.0;
     } else {
-      memcpy(unew, w, sizeof(double) * n);
+      vcopy(n, w, unew);
       scal(n, 1.0 / beta, unew);
     }
     col[3 * p] = beta; /* h_{j+p,j} */
@@ -394,12 +435,13 @@ int oracle_bminres(int64_t n, const int32_t* rowptr, const int32_t* colidx, cons
 
     /* ---- search direction, Eq. (search-dir-comp): m_j = (u_j - sum r_{i,j} m_i) / r_jj ---- */
     double* mj = MSLOT(j);
-    memcpy(mj, USLOT(j), sizeof(double) * n);
+    vcopy(n, USLOT(j), mj);
     for (int i = (j - 2 * p > 1 ? j - 2 * p : 1); i <= j - 1; ++i)
       axpy(n, -col[i - j + 2 * p], MSLOT(i), mj);
     scal(n, 1.0 / rjj, mj);
     /* ---- progressive update, Eq. (approx-update): X_j = X_{j-1} + m_j z_j^T ---- */
     for (int b = 0; b < p; ++b) z[b] = Shat[0 * p + b];
+    OMP_FOR
     for (int64_t r = 0; r < n; ++r) {
       double mr = mj[r];
       for (int b = 0; b < p; ++b) X[r * p + b] += mr * z[b];

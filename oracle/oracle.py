@@ -15,21 +15,36 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bminres_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
+# build variants of the one source: the parity oracle (plain FP64), the same arithmetic with
+# inner products and matvec sums accumulated in long double (a second reference that differs only in
+# summation rounding), and the all-core OpenMP build used only to time the oracle on the host
+_VARIANTS = {
+    "fp64": ("liboracle.so", []),
+    "ext": ("liboracle_ext.so", ["-DORACLE_ACC=long double"]),
+    "omp": ("liboracle_omp.so", ["-fopenmp", "-DORACLE_OMP"]),
+}
 _SO = os.path.join(_BUILD, "liboracle.so")
 
 STATUS = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_INVALID", -3: "ERR_OOM", -4: "ERR_BREAKDOWN",
           -5: "ERR_BENCH_EXHAUSTED", -6: "ERR_NONFINITE"}
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, variant: str = "fp64") -> str:
     """Compile the oracle with plain IEEE arithmetic (no FMA contraction, no fast-math)."""
+    name, extra = _VARIANTS[variant]
+    so = os.path.join(_BUILD, name)
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        tmp = _SO + ".tmp%d" % os.getpid()
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
+        tmp = so + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _SO)
-    return _SO
+                               *extra, "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, so)
+    return so
+
+
+def build_all(force: bool = False) -> None:
+    for v in _VARIANTS:
+        build(force, v)
 
 
 class _Info(ctypes.Structure):
@@ -37,25 +52,25 @@ class _Info(ctypes.Structure):
                 ("setup_deflations", ctypes.c_int), ("bench_used", ctypes.c_int)]
 
 
-_lib = None
+_libs = {}
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        _lib = ctypes.CDLL(build())
+def _load(variant: str = "fp64"):
+    if variant not in _libs:
+        lib = ctypes.CDLL(build(variant=variant))
         P = ctypes.c_void_p
-        _lib.oracle_bminres.restype = ctypes.c_int
-        _lib.oracle_bminres.argtypes = [
+        lib.oracle_bminres.restype = ctypes.c_int
+        lib.oracle_bminres.argtypes = [
             ctypes.c_int64, P, P, P, ctypes.c_int, P, P, ctypes.c_double, ctypes.c_int,
             ctypes.c_double, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
             ctypes.c_int, P, P, P, ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int, P, P,
             ctypes.POINTER(_Info)]
-        _lib.oracle_bench_value.restype = ctypes.c_double
-        _lib.oracle_bench_value.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
-        _lib.oracle_csr_spmm.restype = None
-        _lib.oracle_csr_spmm.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int, P, P]
-    return _lib
+        lib.oracle_bench_value.restype = ctypes.c_double
+        lib.oracle_bench_value.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
+        lib.oracle_csr_spmm.restype = None
+        lib.oracle_csr_spmm.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int, P, P]
+        _libs[variant] = lib
+    return _libs[variant]
 
 
 def _ptr(a):
@@ -84,9 +99,12 @@ class Result:
 
 
 def bminres(A, B, X0=None, tol=1e-10, maxit=1000, gamma=1e-8, bench=4, seed=0, ghost=False,
-            qr="householder", hist=0, xhist=0, uhist=0) -> Result:
-    """Run the oracle on CSR ``A`` (a ``workloads.CSR``) and row-major ``B`` (n, p)."""
-    lib = _load()
+            qr="householder", hist=0, xhist=0, uhist=0, variant="fp64") -> Result:
+    """Run the oracle on CSR ``A`` (a ``workloads.CSR``) and row-major ``B`` (n, p).
+
+    ``variant``: "fp64" (the parity oracle), "ext" (long-double accumulation of the sums) or
+    "omp" (all host cores; for timing)."""
+    lib = _load(variant)
     n = A.n
     B = np.ascontiguousarray(B, dtype=np.float64)
     if B.ndim == 1:

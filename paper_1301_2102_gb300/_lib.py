@@ -13,10 +13,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libbminres.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "bminres.h")
 
-STATUS = {0: "BMINRES_OK", 1: "BMINRES_NOT_CONVERGED", -1: "BMINRES_ERR_INVALID", -2: "BMINRES_ERR_CUDA",
+STATUS = {0: "BMINRES_OK", 1: "BMINRES_NOT_CONVERGED", 2: "BMINRES_RESIDUAL_GAP", -1: "BMINRES_ERR_INVALID",
+          -2: "BMINRES_ERR_CUDA",
           -3: "BMINRES_ERR_OOM", -4: "BMINRES_ERR_BREAKDOWN", -5: "BMINRES_ERR_BENCH_EXHAUSTED",
           -6: "BMINRES_ERR_NONFINITE", -7: "BMINRES_ERR_TIMEOUT"}
-OK, NOT_CONVERGED = 0, 1
+OK, NOT_CONVERGED, RESIDUAL_GAP = 0, 1, 2
 FP64, MIXED, MIXED_DW, FP64_REFINED = 0, 1, 2, 3
 
 
@@ -80,6 +81,8 @@ def load() -> ctypes.CDLL:
     lib.bminres_get_history.restype = I
     lib.bminres_destroy.argtypes = [P]
     lib.bminres_destroy.restype = None
+    lib.bminres_fp64_peak.argtypes = [I, P, ctypes.POINTER(D), ctypes.POINTER(D)]
+    lib.bminres_fp64_peak.restype = I
     lib.bminres_status_string.argtypes = [I]
     lib.bminres_status_string.restype = ctypes.c_char_p
     _lib = lib
@@ -90,3 +93,12 @@ def default_opts() -> Opts:
     o = Opts()
     load().bminres_default_opts(ctypes.byref(o))
     return o
+
+
+def fp64_peak_gflops(iters: int = 200000, stream=None) -> tuple[float, float]:
+    """Measured FP64 FMA throughput of the current GPU (GFLOP/s) and the timed launch's ms."""
+    g, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = load().bminres_fp64_peak(int(iters), ctypes.c_void_p(stream or 0), ctypes.byref(g), ctypes.byref(ms))
+    if st != OK:
+        raise BminresError(st, "bminres_fp64_peak")
+    return g.value, ms.value

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbminres.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
-SOURCES = ["bminres_api.cu", "bminres_noalloc.cu", "solver_f64_a.cu", "solver_f64_b.cu", "solver_f64_c.cu", "solver_f32_a.cu",
+SOURCES = ["bminres_api.cu", "bminres_noalloc.cu", "peak_probe.cu", "solver_f64_a.cu", "solver_f64_b.cu", "solver_f64_c.cu", "solver_f32_a.cu",
            "solver_f32_b.cu", "solver_f32_c.cu", "solver_dw_a.cu", "solver_dw_b.cu"]
 
 

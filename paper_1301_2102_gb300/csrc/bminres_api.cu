@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <initializer_list>
 #include <type_traits>
 #include <cstdint>
 #include <cstdio>
@@ -17,6 +18,7 @@
 #include "../../include/bminres.h"
 #include "aux_kernels.cuh"
 #include "launch.cuh"
+#include "pointer_kind.h"
 
 namespace bmr {
 
@@ -81,14 +83,26 @@ bminres_status from_cuda(cudaError_t e) {
     if (_e != cudaSuccess) return from_cuda(_e); \
   } while (0)
 
-bool is_device_ptr(const void* p) {
-  if (!p) return false;
+// Where a caller's pointer lives: host memory (pageable or pinned), device or managed memory of
+// the current device, or memory of another device (rejected).
+using Mem = bmr::MemKind;
+static_assert(cudaMemoryTypeDevice == 2 && cudaMemoryTypeManaged == 3, "memory type numbering of mem_kind");
+Mem classify(const void* p) {
   cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+  if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return Mem::host;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError();
+  return bmr::mem_kind(true, (int)at.type, at.device, dev);
+}
+bool is_device_ptr(const void* p) { return classify(p) == Mem::device; }
+// true if any of the pointers is device memory of another GPU
+bool foreign(std::initializer_list<const void*> ps) {
+  for (const void* p : ps)
+    if (p && classify(p) == Mem::other_device) return true;
+  return false;
 }
 
 int pm_for(int p) {
@@ -431,7 +445,6 @@ bminres_status solve_device(bminres_handle h, int p, const double* B, double* X,
     st = refine<double>(h, p, B, X, tol, maxit, s, f0, inf);
   }
   // FP64 true residual of the result
-  st = (st == BMINRES_OK || st == BMINRES_NOT_CONVERGED) ? st : st;
   {
     bminres_status rs = prec == 1   ? residual<float>(h, p, B, X, (float*)w.F, s, true)
                         : prec == 2 ? residual<bmr::dw>(h, p, B, X, (bmr::dw*)w.F, s, true)
@@ -444,6 +457,8 @@ bminres_status solve_device(bminres_handle h, int p, const double* B, double* X,
       worst = std::max(worst, rel);
     }
     inf.relres_true_max = worst;
+    // FP64 mode stops on the recursive residual (Eq. (comp-resid)); say so when the true one missed
+    if (prec == 0 && st == BMINRES_OK && worst > tol) st = BMINRES_RESIDUAL_GAP;
   }
   BMR_TRY(cudaEventRecord(h->ev1, s));
   BMR_TRY(cudaEventSynchronize(h->ev1));
@@ -477,6 +492,7 @@ const char* bminres_status_string(bminres_status s) {
   switch (s) {
     case BMINRES_OK: return "BMINRES_OK";
     case BMINRES_NOT_CONVERGED: return "BMINRES_NOT_CONVERGED";
+    case BMINRES_RESIDUAL_GAP: return "BMINRES_RESIDUAL_GAP";
     case BMINRES_ERR_INVALID: return "BMINRES_ERR_INVALID";
     case BMINRES_ERR_CUDA: return "BMINRES_ERR_CUDA";
     case BMINRES_ERR_OOM: return "BMINRES_ERR_OOM";
@@ -494,6 +510,7 @@ bminres_status bminres_create(bminres_handle* out, int64_t n, int64_t nnz, const
   *out = nullptr;
   if (n < 0 || nnz < 0 || nnz >= ((int64_t)1 << 31) || n >= ((int64_t)1 << 31)) return BMINRES_ERR_INVALID;
   if (!rowptr || (nnz > 0 && (!colidx || !vals))) return BMINRES_ERR_INVALID;
+  if (foreign({rowptr, colidx, vals})) return BMINRES_ERR_INVALID;
   bminres_opts o;
   bminres_default_opts(&o);
   if (opts) o = *opts;
@@ -576,7 +593,7 @@ bminres_status bminres_create(bminres_handle* out, int64_t n, int64_t nnz, const
 bminres_status bminres_set_values(bminres_handle h, const double* vals, bminres_stream stream) {
   if (!h) return BMINRES_ERR_INVALID;
   if (h->nnz == 0) return BMINRES_OK;
-  if (!vals) return BMINRES_ERR_INVALID;
+  if (!vals || foreign({vals})) return BMINRES_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   BMR_TRY(cudaMemcpyAsync(h->vals, vals, sizeof(double) * h->nnz, cudaMemcpyDefault, s));
   const int cb = (int)std::min<int64_t>((h->nnz + 255) / 256, 4096);
@@ -617,6 +634,7 @@ bminres_status bminres_solve(bminres_handle h, int p, const double* B, double* X
   if (!h) return BMINRES_ERR_INVALID;
   if (h->n == 0 || p == 0) return BMINRES_OK;
   if (p < 0 || p > PMAX || p > h->n || !B || !X || !(tol > 0.0) || maxit < 0) return BMINRES_ERR_INVALID;
+  if (foreign({B, X})) return BMINRES_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   const bool dB = is_device_ptr(B), dX = is_device_ptr(X);
   if (dB && dX) return solve_device(h, p, B, X, tol, maxit, s, relres_true, info);
@@ -629,7 +647,7 @@ bminres_status bminres_solve(bminres_handle h, int p, const double* B, double* X
   if (!dB) BMR_TRY(cudaMemcpyAsync(Bd, B, bytes, cudaMemcpyHostToDevice, s));
   if (!dX) BMR_TRY(cudaMemcpyAsync(Xd, X, bytes, cudaMemcpyHostToDevice, s));
   st = solve_device(h, p, Bd, Xd, tol, maxit, s, relres_true, info);
-  if (st != BMINRES_OK && st != BMINRES_NOT_CONVERGED) return st;
+  if (st != BMINRES_OK && st != BMINRES_NOT_CONVERGED && st != BMINRES_RESIDUAL_GAP) return st;
   if (!dX) {
     BMR_TRY(cudaMemcpyAsync(X, Xd, bytes, cudaMemcpyDeviceToHost, s));
     BMR_TRY(cudaStreamSynchronize(s));
@@ -665,6 +683,7 @@ bminres_status bminres_spmm(bminres_handle h, int p, const double* X, double* Y,
   if (!h) return BMINRES_ERR_INVALID;
   if (h->n == 0 || p == 0) return BMINRES_OK;
   if (p < 0 || p > PMAX || !X || !Y) return BMINRES_ERR_INVALID;
+  if (foreign({X, Y})) return BMINRES_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   const bool dx = is_device_ptr(X), dy = is_device_ptr(Y);
   const size_t bytes = sizeof(double) * h->n * p;
@@ -692,6 +711,7 @@ bminres_status bminres_backward(bminres_handle h, int p, const double* G, const 
   if (!h) return BMINRES_ERR_INVALID;
   if (h->n == 0 || p == 0) return BMINRES_OK;
   if (p < 0 || p > PMAX || !G || !dB || (dA_vals && !X) || !(tol > 0.0) || maxit < 0) return BMINRES_ERR_INVALID;
+  if (foreign({G, X, dB, dA_vals})) return BMINRES_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = sizeof(double) * h->n * p;
   // dB = A^{-1} G by a block solve from zero (A symmetric, so A^{-T} = A^{-1})
@@ -709,7 +729,7 @@ bminres_status bminres_backward(bminres_handle h, int p, const double* G, const 
   cudaError_t e = cudaMemsetAsync(dBd, 0, bytes, s);
   if (e != cudaSuccess) st = from_cuda(e);
   if (st == BMINRES_OK) st = solve_device(h, p, Gd, dBd, tol, maxit, s, nullptr, info);
-  if (st == BMINRES_OK || st == BMINRES_NOT_CONVERGED) {
+  if (st == BMINRES_OK || st == BMINRES_NOT_CONVERGED || st == BMINRES_RESIDUAL_GAP) {
     bminres_status keep = st;
     if (dA_vals) {
       bmr::sddmm_kernel<<<(int)((h->n + bmr::AUX_NT - 1) / bmr::AUX_NT), bmr::AUX_NT, 0, s>>>(h->n, p, h->rowptr,

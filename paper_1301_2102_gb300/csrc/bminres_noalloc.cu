@@ -14,6 +14,7 @@
 #include "../../include/bminres.h"
 #include "aux_kernels.cuh"
 #include "launch.cuh"
+#include "pointer_kind.h"
 
 namespace {
 
@@ -42,13 +43,17 @@ cudaError_t scratch_address(void** out) {
   return cudaSuccess;
 }
 
+// true for device memory of the current device (or managed memory); false for host memory and
+// for memory of another GPU, which the kernels cannot read without peer access
 bool on_device(const void* p) {
   cudaPointerAttributes at;
   if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError();
+  return bmr::mem_kind(true, (int)at.type, at.device, dev) == bmr::MemKind::device;
 }
 
 int pm_of(int p) {
@@ -93,7 +98,7 @@ int nvmax_of(int pm) {
   return 0;
 }
 
-size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 bminres_status status_of(int st) {
   switch (st) {
@@ -143,8 +148,14 @@ extern "C" bminres_status bminres_solve_noalloc(int64_t n, int64_t nnz, const in
       std::max<int64_t>(1, std::min<int64_t>((int64_t)bps * num_sms, (n + 511) / 512));
   const int grid = (int)(o.max_blocks > 0 ? std::min<int64_t>(grid64, o.max_blocks) : grid64);
   const int nres = (int)((n + bmr::AUX_NT - 1) / bmr::AUX_NT);
+  // the control block and both sets of column norms sit side by side, so that one copy at the end
+  // brings every result the host needs
   size_t off = 0;
   const size_t oCtl = off; off += align256(sizeof(bmr::Ctl));
+  const size_t oNo0 = off; off += sizeof(double) * 64;  // ||f0_i||
+  const size_t oNo1 = off; off += sizeof(double) * 64;  // ||b_i - A x_i|| after the solve
+  const size_t tail_bytes = off;
+  off = align256(off);
   const size_t oU = off; off += align256(sizeof(double) * 2 * p * ld);
   const size_t oW = off; off += align256(sizeof(double) * p * ld);
   const size_t oM = off; off += align256(sizeof(double) * 2 * p * ld);
@@ -153,7 +164,6 @@ extern "C" bminres_status bminres_solve_noalloc(int64_t n, int64_t nnz, const in
   const size_t oF = off; off += align256(sizeof(double) * p * ld);
   const size_t oP = off; off += align256(sizeof(double) * 2 * (size_t)nvmax_of(pm) * grid);
   const size_t oN = off; off += align256(sizeof(double) * (size_t)p * nres);
-  const size_t oNo = off; off += align256(sizeof(double) * 64);
   if (off > BMINRES_NOALLOC_SCRATCH_BYTES) return BMINRES_ERR_INVALID;  // does not fit the array
   if (!on_device(rowptr) || (nnz > 0 && (!on_device(colidx) || !on_device(vals))) || !on_device(B) ||
       !on_device(X))
@@ -171,7 +181,8 @@ extern "C" bminres_status bminres_solve_noalloc(int64_t n, int64_t nnz, const in
   double* F = reinterpret_cast<double*>(sb + oF);
   double* part = reinterpret_cast<double*>(sb + oP);
   double* npart = reinterpret_cast<double*>(sb + oN);
-  double* norms = reinterpret_cast<double*>(sb + oNo);
+  double* norms0 = reinterpret_cast<double*>(sb + oNo0);
+  double* norms1 = reinterpret_cast<double*>(sb + oNo1);
   cudaStream_t s = (cudaStream_t)stream;
 
   // the array keeps the previous call's contents: clear what the solve expects to start at zero
@@ -181,12 +192,10 @@ extern "C" bminres_status bminres_solve_noalloc(int64_t n, int64_t nnz, const in
   NA_TRY(cudaMemsetAsync(ctl, 0, sizeof(bmr::Ctl), s));
 
   // F0 = B - A X0 (FP64) and its column norms
-  double f0[32], rt[32];
   bmr::residual_kernel<double><<<nres, bmr::AUX_NT, 0, s>>>(n, p, rowptr, colidx, vals, B, X, F, ld, npart);
   NA_TRY(cudaGetLastError());
-  bmr::finish_norms_kernel<<<1, bmr::AUX_NT, 0, s>>>(p, nres, npart, norms);
+  bmr::finish_norms_kernel<<<1, bmr::AUX_NT, 0, s>>>(p, nres, npart, norms0);
   NA_TRY(cudaGetLastError());
-  NA_TRY(cudaMemcpyAsync(f0, norms, sizeof(double) * p, cudaMemcpyDeviceToHost, s));
 
   bmr::SolveArgs<double> a;
   memset(&a, 0, sizeof(a));
@@ -213,16 +222,20 @@ extern "C" bminres_status bminres_solve_noalloc(int64_t n, int64_t nnz, const in
   a.ctl = ctl;
   a.barrier_limit_ns = 10ull * 1000 * 1000 * 1000;
   NA_TRY(launch_f64(pm, a, grid, s));
-  bmr::Ctl r;
-  NA_TRY(cudaMemcpyAsync(&r, ctl, sizeof(bmr::Ctl), cudaMemcpyDeviceToHost, s));
 
   // FP64 true residual of the result
   bmr::residual_kernel<double><<<nres, bmr::AUX_NT, 0, s>>>(n, p, rowptr, colidx, vals, B, X, F, ld, npart);
   NA_TRY(cudaGetLastError());
-  bmr::finish_norms_kernel<<<1, bmr::AUX_NT, 0, s>>>(p, nres, npart, norms);
+  bmr::finish_norms_kernel<<<1, bmr::AUX_NT, 0, s>>>(p, nres, npart, norms1);
   NA_TRY(cudaGetLastError());
-  NA_TRY(cudaMemcpyAsync(rt, norms, sizeof(double) * p, cudaMemcpyDeviceToHost, s));
+  // one copy of the control block and both norm sets (a stack buffer: nothing is allocated)
+  alignas(16) unsigned char tail[align256(sizeof(bmr::Ctl)) + 2 * 64 * sizeof(double)];
+  NA_TRY(cudaMemcpyAsync(tail, sb + oCtl, tail_bytes, cudaMemcpyDeviceToHost, s));
   NA_TRY(cudaStreamSynchronize(s));
+  bmr::Ctl r;
+  memcpy(&r, tail, sizeof(bmr::Ctl));
+  const double* f0 = reinterpret_cast<const double*>(tail + oNo0);
+  const double* rt = reinterpret_cast<const double*>(tail + oNo1);
 
   double worst = 0.0;
   for (int i = 0; i < p; ++i) {
@@ -230,7 +243,9 @@ extern "C" bminres_status bminres_solve_noalloc(int64_t n, int64_t nnz, const in
     if (relres_true) relres_true[i] = rel;
     worst = std::max(worst, rel);
   }
-  const bminres_status st = status_of(r.status);
+  bminres_status st = status_of(r.status);
+  // the solve stops on the recursive residual (Eq. (comp-resid)); say so when the true one missed
+  if (st == BMINRES_OK && worst > tol) st = BMINRES_RESIDUAL_GAP;
   if (info) {
     info->status = st;
     info->iters = r.iters;

@@ -28,7 +28,9 @@ def _as_ptr(x):
 
 
 def _check(st: int, what: str, allow_not_converged: bool = True) -> int:
-    if st == _lib.OK or (allow_not_converged and st == _lib.NOT_CONVERGED):
+    """Raise for error statuses.  NOT_CONVERGED and RESIDUAL_GAP (the recursive residual met tol
+    but the FP64 true residual did not) leave a usable iterate and are reported, not raised."""
+    if st == _lib.OK or (allow_not_converged and st in (_lib.NOT_CONVERGED, _lib.RESIDUAL_GAP)):
         return st
     raise _lib.BminresError(st, what)
 
@@ -106,7 +108,8 @@ class Solver:
 
         Returns ``(X, info, relres_true)``: ``info`` is a dict of the C info struct and
         ``relres_true`` the per-column FP64 ``||b_i - A x_i|| / ||b_i - A x0_i||``.
-        Raises ``BminresError`` for error statuses; NOT_CONVERGED is reported in ``info``.
+        Raises ``BminresError`` for error statuses; NOT_CONVERGED and RESIDUAL_GAP are reported in
+        ``info``.
         """
         p = 1 if B.ndim == 1 else int(B.shape[1])
         if X is None:

@@ -136,15 +136,60 @@ def randn_rhs(n: int, p: int, seed: int = 0) -> np.ndarray:
     return np.ascontiguousarray(rng.standard_normal((n, p)))
 
 
+def dependent_rhs(n: int, p: int, seed: int = 0) -> np.ndarray:
+    """``p >= 6`` columns: 0..p-3 N(0,1); column p-2 = 0.5 c0 - 1.2 c3 + 1e-12 N(0,1); column p-1 =
+    c1 + c2 exactly (the benchmark's dependence structure, widened to p columns)."""
+    if p < 6:
+        raise ValueError("p must be at least 6")
+    rng = np.random.default_rng(seed)
+    B = np.empty((n, p))
+    B[:, : p - 2] = rng.standard_normal((n, p - 2))
+    noise = rng.standard_normal(n)
+    B[:, p - 2] = 0.5 * B[:, 0] - 1.2 * B[:, 3] + 1e-12 * noise
+    B[:, p - 1] = B[:, 1] + B[:, 2]
+    return np.ascontiguousarray(B)
+
+
 def dependent_rhs_p8(n: int, seed: int = 0) -> np.ndarray:
     """Eight columns: 0-5 N(0,1); col6 = 0.5 c0 - 1.2 c3 + 1e-12 N(0,1); col7 = c1 + c2 exactly."""
+    return dependent_rhs(n, 8, seed)
+
+
+def near_dependent_dense(n: int, p: int, seed: int = 11) -> tuple[CSR, np.ndarray]:
+    """Dense symmetric indefinite operator (eigenvalues +-[0.6, 4], every third one negative) and p
+    right-hand sides whose first column lies within 1e-14 of a 3-dimensional invariant subspace: the
+    block Krylov sequence started from it becomes dependent after a few iterations (Sec. 5)."""
     rng = np.random.default_rng(seed)
-    B = np.empty((n, 8))
-    B[:, :6] = rng.standard_normal((n, 6))
-    noise = rng.standard_normal(n)
-    B[:, 6] = 0.5 * B[:, 0] - 1.2 * B[:, 3] + 1e-12 * noise
-    B[:, 7] = B[:, 1] + B[:, 2]
-    return np.ascontiguousarray(B)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.linspace(0.6, 4.0, n) * np.where(np.arange(n) % 3 == 0, -1.0, 1.0)
+    D = (Q * lam) @ Q.T
+    A = dense_to_csr(0.5 * (D + D.T))
+    f1 = Q[:, :3] @ np.array([1.0, -0.7, 0.4]) + 1e-14 * rng.standard_normal(n)
+    B = np.concatenate([f1[:, None], rng.standard_normal((n, p - 1))], axis=1)
+    return A, np.ascontiguousarray(B)
+
+
+def laplacian_mode_3d(N: int, k: tuple[int, int, int]) -> np.ndarray:
+    """Normalised eigenvector ``sin(k_x x pi/(N+1)) sin(k_y y pi/(N+1)) sin(k_z z pi/(N+1))`` of the
+    3D stencil (lexicographic order, x fastest)."""
+    th = math.pi / (N + 1)
+    t = np.arange(1, N + 1)
+    sx, sy, sz = (np.sin(kk * t * th) for kk in k)
+    q = (sz[:, None, None] * sy[None, :, None] * sx[None, None, :]).reshape(-1)
+    return q / np.linalg.norm(q)
+
+
+def near_dependent_laplacian(N: int, p: int, seed: int = 11, frac: float = 0.10) -> tuple[CSR, np.ndarray]:
+    """3D shifted Laplacian and p right-hand sides whose first column lies within 1e-14 of the span of
+    three closed-form eigenvectors: the band Krylov sequence it starts is near-dependent after a few
+    cycles (Sec. 5); the other columns are N(0,1)."""
+    A = laplacian(N, 3, shift_at_fraction(N, 3, frac))
+    rng = np.random.default_rng(seed)
+    f1 = (laplacian_mode_3d(N, (1, 2, 1)) - 0.7 * laplacian_mode_3d(N, (3, 1, 2))
+          + 0.4 * laplacian_mode_3d(N, (2, 2, 5)))
+    f1 = f1 + 1e-14 * rng.standard_normal(A.n)
+    B = np.concatenate([f1[:, None], rng.standard_normal((A.n, p - 1))], axis=1)
+    return A, np.ascontiguousarray(B)
 
 
 def saddle_point(NK: int = 512, m: int = 65536, nnz_per_row: int = 4, seed: int = 1) -> CSR:

@@ -68,7 +68,7 @@ def test_reference_arm_under_torchrun_prints_one_line():
     env = dict(os.environ, BMINRES_BENCH_BACKEND="gloo")
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py", "--impl", "reference",
-           "--grid", "10", "--cpu-sample-iters", "2", "--steps", "1"]
+           "--grid", "10", "--ref-sample-iters", "2", "--steps", "2", "--warmup", "1"]
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
@@ -76,6 +76,7 @@ def test_reference_arm_under_torchrun_prints_one_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["extrapolated"] is True and d["steps"] == 2 and d["cpu_baseline"]["cores"] >= 1
 
 
 def test_paper_e1_operator():

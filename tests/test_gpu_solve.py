@@ -1,25 +1,16 @@
 """GPU parity: the CUDA block MINRES (through the C ABI) against the FP64 CPU oracle on the same
-seeded inputs.  Bars: relative residual <= tol; ||X_gpu - X_oracle|| / ||X_oracle|| <= 1e-7 in FP64
-(where kappa * tol allows it); recursive-residual histories equal to 1e-10 relative until the
-rounding of the two orthogonalisation orders is amplified; iteration counts within ITER_TOL.
-
-Iteration counts: the oracle orthogonalises by modified Gram-Schmidt, the GPU by classical inner
-products converted to the same coefficients through the Gram entries.  Both are exact in exact
-arithmetic and the residual histories agree to ~1e-15 until a Ritz value converges; after that,
-finite-precision Lanczos amplifies rounding differences (two CPU MINRES codes, the oracle and
-scipy's, drift apart the same way), so the iteration at which 1e-10 is first met can differ by a
-few percent.  In every case run so far the GPU, whose inner products are tree-summed and so
-slightly more accurate than the oracle's sequential sums, met the tolerance 1-5% earlier.  The bar
-is |d| <= max(2, 5% of the oracle's count).
+seeded inputs.  Bars (tests/_parity.py): FP64 true relative residual <= tol with status OK (or the
+residual-gap status where the oracle's own result misses tol too); ||X_gpu - X_oracle|| /
+||X_oracle|| <= 1e-7 in FP64; recursive-residual histories equal to 1e-10 relative before rounding
+is amplified; iteration counts within +-2 of the interval spanned by the oracle and its
+extended-accumulation build (the spread that summation rounding alone causes on each case).
 """
 import numpy as np
 import pytest
 
+from _parity import check_fp64_result, iter_bracket, iters_ok, oracle_pair, rel_err, true_relres
+
 pytestmark = pytest.mark.gpu
-
-
-def iters_close(gpu, ref):
-    return abs(gpu - ref) <= max(2, int(0.05 * ref))
 
 
 @pytest.fixture(scope="module")
@@ -61,11 +52,10 @@ def test_spmm_matches_csr_order(torch_cuda, oracle_mod, workloads):
 def test_parity_2d_small(torch_cuda, oracle_mod, workloads, p):
     A = workloads.laplacian(20, 2, workloads.shift_at_fraction(20, 2, 0.2))
     B = workloads.randn_rhs(A.n, p, 1)
-    ref = oracle_mod.bminres(A, B, tol=1e-10, maxit=20000)
+    ref, ext = oracle_pair(oracle_mod, A, B, tol=1e-10, maxit=20000)
     X, info, rel = _solve(torch_cuda, A, B)
-    assert info["status"] == 0, info
-    assert rel.max() <= 1e-10 * 1.5
-    assert iters_close(info["iters"], ref.iters), (info["iters"], ref.iters)
+    check_fp64_result(info, rel, true_relres(oracle_mod, A, B, ref.X).max(), 1e-10)
+    assert iters_ok(info["iters"], ref, ext), (info["iters"], iter_bracket(ref, ext))
     assert np.linalg.norm(X - ref.X) / np.linalg.norm(ref.X) <= 1e-7
 
 
@@ -73,11 +63,10 @@ def test_parity_config1_projected(torch_cuda, oracle_mod, workloads):
     A, B = workloads.config_c1()
     Q = workloads.laplacian_null_modes_2d(32, 4.0)
     Bp = workloads.project_out(B, Q)
-    ref = oracle_mod.bminres(A, Bp, tol=1e-10, maxit=4000)
+    ref, ext = oracle_pair(oracle_mod, A, Bp, tol=1e-10, maxit=4000)
     X, info, rel = _solve(torch_cuda, A, Bp, maxit=4000)
-    assert info["status"] == 0
-    assert rel.max() <= 2e-10
-    assert iters_close(info["iters"], ref.iters), (info["iters"], ref.iters)
+    check_fp64_result(info, rel, true_relres(oracle_mod, A, Bp, ref.X).max(), 1e-10)
+    assert iters_ok(info["iters"], ref, ext), (info["iters"], iter_bracket(ref, ext))
     Xr = X - Q @ (Q.T @ X)
     Rr = ref.X - Q @ (Q.T @ ref.X)
     assert np.linalg.norm(Xr - Rr) / np.linalg.norm(Rr) <= 1e-7
@@ -87,11 +76,10 @@ def test_parity_config1_projected(torch_cuda, oracle_mod, workloads):
 def test_parity_3d_ragged(torch_cuda, oracle_mod, workloads, p):
     A = workloads.laplacian(13, 3, workloads.shift_at_fraction(13, 3, 0.1))  # n = 2197, not a tile multiple
     B = workloads.randn_rhs(A.n, p, 2)
-    ref = oracle_mod.bminres(A, B, tol=1e-10, maxit=40000)
+    ref, ext = oracle_pair(oracle_mod, A, B, tol=1e-10, maxit=40000)
     X, info, rel = _solve(torch_cuda, A, B, maxit=40000)
-    assert info["status"] == 0
-    assert rel.max() <= 1.5e-10
-    assert iters_close(info["iters"], ref.iters), (info["iters"], ref.iters)
+    check_fp64_result(info, rel, true_relres(oracle_mod, A, B, ref.X).max(), 1e-10)
+    assert iters_ok(info["iters"], ref, ext), (info["iters"], iter_bracket(ref, ext))
     kappa_tol = 1e-7
     assert np.linalg.norm(X - ref.X) / np.linalg.norm(ref.X) <= kappa_tol
 
@@ -100,12 +88,11 @@ def test_parity_setup_deflation(torch_cuda, oracle_mod, workloads):
     """Config-2 right-hand-side structure on a 12^3 grid: two columns dependent at set-up."""
     A = workloads.laplacian(12, 3, workloads.shift_at_fraction(12, 3, 0.10))
     B = workloads.dependent_rhs_p8(A.n, seed=0)
-    ref = oracle_mod.bminres(A, B, tol=1e-10, maxit=40000, bench=4)
+    ref, ext = oracle_pair(oracle_mod, A, B, tol=1e-10, maxit=40000, bench=4)
     X, info, rel = _solve(torch_cuda, A, B, maxit=40000, bench=4)
     assert ref.setup_deflations == 2 and info["setup_deflations"] == 2
-    assert info["status"] == 0
-    assert rel.max() <= 1.5e-10
-    assert iters_close(info["iters"], ref.iters), (info["iters"], ref.iters)
+    check_fp64_result(info, rel, true_relres(oracle_mod, A, B, ref.X).max(), 1e-10)
+    assert iters_ok(info["iters"], ref, ext), (info["iters"], iter_bracket(ref, ext))
     assert np.linalg.norm(X - ref.X) / np.linalg.norm(ref.X) <= 1e-7
 
 
@@ -115,12 +102,12 @@ def test_parity_dependence_demo(torch_cuda, oracle_mod, workloads):
     e1 = np.zeros(A.n)
     e1[0] = 1.0
     B = np.stack([e1, oracle_mod.spmm(A, e1[:, None])[:, 0]], axis=1)
-    ref = oracle_mod.bminres(A, B, tol=1e-10, maxit=4000)
+    ref, ext = oracle_pair(oracle_mod, A, B, tol=1e-10, maxit=4000)
     X, info, rel = _solve(torch_cuda, A, B, maxit=4000)
     assert ref.defl_iters[0] == 1 and info["deflations"] >= 1
-    assert info["status"] == 0
+    check_fp64_result(info, rel, true_relres(oracle_mod, A, B, ref.X).max(), 1e-10)
     assert np.linalg.norm(X[:, 1] - e1) <= 1e-12
-    assert iters_close(info["iters"], ref.iters), (info["iters"], ref.iters)
+    assert iters_ok(info["iters"], ref, ext), (info["iters"], iter_bracket(ref, ext))
     assert np.linalg.norm(X - ref.X) / np.linalg.norm(ref.X) <= 1e-7
 
 
@@ -131,11 +118,12 @@ def test_parity_nonzero_x0_and_zero_column(torch_cuda, oracle_mod, workloads):
     B[:, 1] = 0.0
     X0 = 0.1 * workloads.randn_rhs(A.n, 3, 5)
     X0[:, 1] = 0.0
-    ref = oracle_mod.bminres(A, B, X0=X0, tol=1e-10, maxit=4000)
+    ref, ext = oracle_pair(oracle_mod, A, B, X0=X0, tol=1e-10, maxit=4000)
     X, info, rel = _solve(torch_cuda, A, B, X0=X0, maxit=4000)
-    assert info["status"] == 0 and info["setup_deflations"] == 1
+    assert info["setup_deflations"] == 1
+    check_fp64_result(info, rel, true_relres(oracle_mod, A, B, ref.X, X0).max(), 1e-10)
     assert np.all(X[:, 1] == 0.0)
-    assert iters_close(info["iters"], ref.iters), (info["iters"], ref.iters)
+    assert iters_ok(info["iters"], ref, ext), (info["iters"], iter_bracket(ref, ext))
     assert np.linalg.norm(X - ref.X) / np.linalg.norm(ref.X) <= 1e-7
 
 
@@ -169,10 +157,10 @@ def test_double_word_inner_solve_matches_oracle(torch_cuda, oracle_mod, workload
     finite-precision Lanczos bar, because ~48-bit vectors keep the recurrence close to FP64's."""
     A = workloads.laplacian(24, 2, workloads.shift_at_fraction(24, 2, 0.15))
     B = workloads.randn_rhs(A.n, p, 11)
-    ref = oracle_mod.bminres(A, B, tol=1e-10, maxit=20000)
+    ref, ext = oracle_pair(oracle_mod, A, B, tol=1e-10, maxit=20000)
     X, info, rel = _solve(torch_cuda, A, B, maxit=20000, precision="mixed_dw", tol_inner=1e-10, max_outer=1)
     assert info["outer"] == 1
-    assert iters_close(info["iters"], ref.iters), (info["iters"], ref.iters)
+    assert iters_ok(info["iters"], ref, ext), (info["iters"], iter_bracket(ref, ext))
     assert np.linalg.norm(X - ref.X) <= 1e-7 * np.linalg.norm(ref.X)
 
 
@@ -237,11 +225,11 @@ def test_parity_near_dependence(torch_cuda, oracle_mod, workloads):
     A = workloads.dense_to_csr(0.5 * (D + D.T))
     f1 = Q[:, :3] @ np.array([1.0, -0.7, 0.4]) + 1e-14 * rng.standard_normal(n)
     B = np.stack([f1, rng.standard_normal(n)], axis=1)
-    ref = oracle_mod.bminres(A, B, tol=1e-10, maxit=3000)
+    ref, ext = oracle_pair(oracle_mod, A, B, tol=1e-10, maxit=3000)
     X, info, rel = _solve(torch_cuda, A, B, maxit=3000)
     assert ref.defl_iters[:1] == [5] and info["deflations"] >= 1
-    assert info["status"] == 0 and rel.max() <= 1.5e-10
-    assert iters_close(info["iters"], ref.iters), (info["iters"], ref.iters)
+    check_fp64_result(info, rel, true_relres(oracle_mod, A, B, ref.X).max(), 1e-10)
+    assert iters_ok(info["iters"], ref, ext), (info["iters"], iter_bracket(ref, ext))
     assert np.linalg.norm(X - ref.X) / np.linalg.norm(ref.X) <= 1e-7
 
 
