@@ -272,8 +272,8 @@ def fp64_peak():
     from paper_1301_2102_gb300 import _lib
 
     best = 0.0
-    for _ in range(3):
-        g, _ms = _lib.fp64_peak_gflops(400000)
+    for _ in range(2):
+        g, _ms = _lib.fp64_peak_gflops(100000)
         best = max(best, g)
     return best
 
@@ -354,7 +354,8 @@ def mode_summary(mode, steps, n, nnz, p, hbm, peak64):
          "status": info["status_name"], "us_per_band_iteration": 1e6 * ks / it,
          "kernel": KERNEL[mode], "gflops": fl * it / ks / 1e9, "hbm_gbs_bmin": by * it / ks / 1e9}
     d["hbm_frac_bmin"] = d["hbm_gbs_bmin"] / hbm
-    d["fp64_frac"] = d["gflops"] / peak64 if peak64 else None
+    if mode in ("fp64", "fp64_refined"):
+        d["fp64_frac"] = d["gflops"] / peak64 if peak64 else None
     d["passes"] = passes_report(info, n, nnz, p, se, 8 if mode in ("fp64", "fp64_refined") else se, hbm)
     return d
 
@@ -534,6 +535,126 @@ def run_paper_e1(args):
     return 0
 
 
+def run_paper_e2(args):
+    """The paper's second experiment on its operator (Sec. 8), unpreconditioned here: for each p, the
+    band iterations of one block solve with right-hand sides [ones, e_1 .. e_{p-1}] against the total
+    of the p single-vector solves, tol 1e-8."""
+    import torch
+
+    from paper_1301_2102_gb300 import Solver, workloads
+
+    A = workloads.paper_e1_operator(200)
+    tol, maxit = 1e-8, 2_000_000
+    ps = [1, 2, 3, 4, 6, 8, 10, 12, 16, 20, 24, 32]
+    Bfull = workloads.ones_identity_rhs(A.n, max(ps))
+    rows = []
+    with Solver(A) as s:
+        Bd = torch.from_numpy(Bfull).cuda()
+        single = []
+        for c in range(max(ps)):
+            _, ic, rc = s.solve(Bd[:, c:c + 1].contiguous(), tol=tol, maxit=maxit)
+            single.append((ic["iters"], ic["device_ms"]))
+        for p in ps:
+            X, info, rel = s.solve(Bd[:, :p].contiguous(), tol=tol, maxit=maxit)
+            seq_it = sum(x[0] for x in single[:p])
+            seq_ms = sum(x[1] for x in single[:p])
+            rows.append({"p": p, "block_iters": info["iters"], "sequential_iters": seq_it,
+                         "iteration_ratio": info["iters"] / seq_it, "block_ms": info["device_ms"],
+                         "sequential_ms": seq_ms, "status": info["status_name"],
+                         "relres_true_max": float(rel.max()), "deflations": info["deflations"],
+                         "setup_deflations": info["setup_deflations"]})
+    print(json.dumps({"experiment": "paper E2 operator, -L - 200 I on 200 x 200, right-hand sides [ones, e_1 .. "
+                                    "e_{p-1}], tol 1e-8, no preconditioner", "n": A.n, "rows": rows}), flush=True)
+    return 0
+
+
+def run_c1_latency(args):
+    """The 32 x 32 singular operator (latency-bound: n = 1024): microseconds per band iteration of the
+    range-projected solve to 1e-10, median of 50 timed solves after 5 warm-up solves, and of the
+    literal run (2000 band iterations, stalls at the least-squares floor)."""
+    import torch
+
+    from paper_1301_2102_gb300 import Solver, workloads
+
+    A, B = workloads.config_c1()
+    Q = workloads.laplacian_null_modes_2d(32, 4.0)
+    out = {"experiment": "config 1: 2D 5-point Laplacian 32x32, sigma = 4 (singular), p = 4, tol 1e-10"}
+    with Solver(A) as s:
+        for name, rhs, maxit in (("projected", workloads.project_out(B, Q), 4000), ("literal", B, 2000)):
+            Bd = torch.from_numpy(rhs).cuda()
+            for _ in range(5):
+                s.solve(Bd, tol=1e-10, maxit=maxit)
+            us, ms = [], []
+            for _ in range(50):
+                X, info, rel = s.solve(Bd, tol=1e-10, maxit=maxit)
+                us.append(1e3 * info["kernel_ms"] / max(info["iters"], 1))
+                ms.append(info["device_ms"])
+            out[name] = {"us_per_band_iteration_median": statistics.median(us), "solve_ms_median": statistics.median(ms),
+                         "band_iterations": info["iters"], "status": info["status_name"],
+                         "relres_true_max": float(rel.max()), "grid_blocks": info["grid_blocks"], "solves_timed": 50}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_c3_sweep(args):
+    """Block-size scaling on the 128^3 operator (p N(0,1) right-hand sides): microseconds per band
+    iteration of capped solves (--sweep-iters band iterations, after one warm-up) per precision, and
+    per right-hand side."""
+    import torch
+
+    from paper_1301_2102_gb300 import Solver, workloads
+
+    N = args.grid
+    A = workloads.laplacian(N, 3, workloads.shift_at_fraction(N, 3, 0.10))
+    rows = []
+    for p in (1, 4, 8, 16):
+        B = torch.from_numpy(workloads.randn_rhs(A.n, p, 0)).cuda()
+        for mode in ("fp64", "mixed_dw", "mixed"):
+            with Solver(A, precision=mode, max_outer=1, tol_inner=1e-12) as s:
+                s.solve(B, tol=1e-12, maxit=200)
+                X, info, rel = s.solve(B, tol=1e-12, maxit=args.sweep_iters)
+            it = max(info["iters"], 1)
+            us = 1e3 * info["kernel_ms"] / it
+            rows.append({"p": p, "mode": mode, "band_iterations": info["iters"], "us_per_band_iteration": us,
+                         "us_per_band_iteration_per_rhs": us / p,
+                         "block_product_us": 1e3 * info["spmm_ms"] / it, "directions_us": 1e3 * info["dir_ms"] / it,
+                         "fused_us": 1e3 * (info["stream_ms"] - info["spmm_ms"] - info["dir_ms"]) / it})
+    print(json.dumps({"experiment": f"config 3 block-size sweep, {N}^3, capped at {args.sweep_iters} band iterations",
+                      "rows": rows}), flush=True)
+    return 0
+
+
+def run_c5(args):
+    """Config 5 (192^3, sigma at 5 % of the spectrum, p = 32 N(0,1) right-hand sides): per band
+    iteration times of the FP64 and FP32-inner forward solves and of the FP64 adjoint solve for
+    L = sum(X^2) (G = 2X), capped at --sweep-iters band iterations, and the device memory in use."""
+    import torch
+
+    from paper_1301_2102_gb300 import Solver, workloads
+
+    A, B0 = workloads.config_c5()
+    B = torch.from_numpy(B0).cuda()
+    out = {"experiment": "config 5: 3D 7-point Laplacian 192^3 shifted at 5%, p = 32, capped solves",
+           "n": A.n, "nnz": A.nnz, "p": 32, "iters_cap": args.sweep_iters}
+    for mode in ("fp64", "mixed"):
+        free0 = torch.cuda.mem_get_info()[0]
+        with Solver(A, precision=mode, max_outer=1, tol_inner=1e-12) as s:
+            s.solve(B, tol=1e-12, maxit=100)
+            X, info, rel = s.solve(B, tol=1e-12, maxit=args.sweep_iters)
+            free1 = torch.cuda.mem_get_info()[0]
+            it = max(info["iters"], 1)
+            d = {"us_per_band_iteration": 1e3 * info["kernel_ms"] / it, "band_iterations": info["iters"],
+                 "relres_true_max": float(rel.max()), "device_bytes_in_use": free0 - free1,
+                 "block_product_us": 1e3 * info["spmm_ms"] / it, "directions_us": 1e3 * info["dir_ms"] / it}
+            if mode == "fp64":
+                dB, dA, binfo = s.backward((2.0 * X).contiguous(), X, tol=1e-12, maxit=args.sweep_iters)
+                d["adjoint_us_per_band_iteration"] = 1e3 * binfo["kernel_ms"] / max(binfo["iters"], 1)
+                d["adjoint_band_iterations"] = binfo["iters"]
+            out[mode] = d
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -556,9 +677,23 @@ def main():
                     help="profiling aid: run one solve capped at this many band iterations and print its info")
     ap.add_argument("--paper-e1", action="store_true",
                     help="run the paper's first experiment on its operator (block vs sequential) and exit")
+    ap.add_argument("--paper-e2", action="store_true",
+                    help="run the paper's second experiment (iteration ratio over p) on its operator and exit")
+    ap.add_argument("--c1-latency", action="store_true", help="config 1 microseconds per band iteration and exit")
+    ap.add_argument("--c3-sweep", action="store_true", help="config 3 block-size sweep (capped solves) and exit")
+    ap.add_argument("--c5", action="store_true", help="config 5 capped forward and adjoint solves and exit")
+    ap.add_argument("--sweep-iters", type=int, default=1500, help="band iterations of the capped solves")
     args = ap.parse_args()
     if args.paper_e1:
         return run_paper_e1(args)
+    if args.paper_e2:
+        return run_paper_e2(args)
+    if args.c1_latency:
+        return run_c1_latency(args)
+    if args.c3_sweep:
+        return run_c3_sweep(args)
+    if args.c5:
+        return run_c5(args)
     if args.profile_iters > 0:
         return run_profile_case(args)
     if args.impl == "reference":

@@ -176,11 +176,12 @@ bminres_status bminres_solve_noalloc(int64_t n, int64_t nnz, const int32_t* rowp
                                      double* relres_true, bminres_info* info);
 
 /* Measurement helper, not a step of the method (the paper has no counterpart): FP64 fused
- * multiply-add throughput of the current GPU, in GFLOP/s (2 flops per FMA), from one timed launch of
- * independent FMA chains (8 blocks of 256 threads per SM, `iters` FMAs per chain and thread, 8
- * chains per thread) after one warm-up launch, on `stream`.  It is the denominator of the arithmetic
- * roofline against which the FP64 solve is reported.  ms (may be NULL) receives the timed launch's
- * duration.  Allocates 8 bytes of device memory for the duration of the call. */
+ * multiply-add throughput of the current GPU, in GFLOP/s (2 flops per FMA): the fastest of three
+ * timed launches of independent FMA chains (8 or 16 chains per thread, 4 or 8 blocks of 256 threads
+ * per SM, about 8 * `iters` FMAs per thread), each after a warm-up launch, on `stream`.  It is the
+ * denominator of the arithmetic roofline against which the FP64 solve is reported.  ms (may be NULL)
+ * receives the fastest timed launch's duration.  Allocates 8 bytes of device memory for the
+ * duration of the call. */
 bminres_status bminres_fp64_peak(int iters, bminres_stream stream, double* gflops, double* ms);
 
 /* Release the handle and everything it owns.  NULL is ignored. */

@@ -50,6 +50,8 @@
  *                double).  `long double` gives a second reference whose only difference is the
  *                rounding of those sums; the tests use it to measure how much the iteration count
  *                at which the tolerance is met depends on summation rounding.
+ *   ORACLE_FMA   vector updates y + a x rounded once (C99 fma) instead of twice; with ORACLE_ACC =
+ *                long double this is the most accurately rounded build of the same steps.
  *   ORACLE_OMP   (with -fopenmp) the vector loops and the matvec run on all host cores, the inner
  *                products as fixed chunks summed in chunk order, so the result does not depend on
  *                the thread count.  Used only to time the oracle on the host cores. */
@@ -121,7 +123,11 @@ static double dot(int64_t n, const double* x, const double* y) {
 }
 static void axpy(int64_t n, double a, const double* x, double* y) {
   OMP_FOR
+#ifdef ORACLE_FMA
+  for (int64_t r = 0; r < n; ++r) y[r] = fma(a, x[r], y[r]);
+#else
   for (int64_t r = 0; r < n; ++r) y[r] += a * x[r];
+#endif
 }
 static double nrm2(int64_t n, const double* x) { return sqrt(dot(n, x, x)); }
 static void scal(int64_t n, double a, double* x) {

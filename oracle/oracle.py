@@ -21,6 +21,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _VARIANTS = {
     "fp64": ("liboracle.so", []),
     "ext": ("liboracle_ext.so", ["-DORACLE_ACC=long double"]),
+    "extfma": ("liboracle_extfma.so", ["-DORACLE_ACC=long double", "-DORACLE_FMA"]),
     "omp": ("liboracle_omp.so", ["-fopenmp", "-DORACLE_OMP"]),
 }
 _SO = os.path.join(_BUILD, "liboracle.so")

@@ -130,6 +130,16 @@ def paper_e1_operator(N: int = 200) -> CSR:
     return laplacian(N, 2, 200.0 * h * h)
 
 
+def ones_identity_rhs(n: int, p: int) -> np.ndarray:
+    """The right-hand sides of the paper's second experiment (Sec. 8): the vector of all ones, then
+    the first p - 1 columns of the identity."""
+    B = np.zeros((n, p))
+    B[:, 0] = 1.0
+    for k in range(1, p):
+        B[k - 1, k] = 1.0
+    return np.ascontiguousarray(B)
+
+
 def randn_rhs(n: int, p: int, seed: int = 0) -> np.ndarray:
     """``(n, p)`` row-major float64 matrix of i.i.d. N(0,1) entries."""
     rng = np.random.default_rng(seed)

@@ -2,10 +2,14 @@
 
 Iteration counts.  The solve stops at the first band iteration whose recursive residual meets tol.
 Once a Ritz value has converged, finite-precision Lanczos amplifies rounding differences, so that
-iteration depends on how the inner products are rounded.  Two oracle builds that differ ONLY in
-the accumulation type of their sums (FP64, and long double: 80-bit on x86, IEEE binary128 on Arm)
-measure that spread on each case; the GPU (tree-summed inner products) must lie within +-2 of the
-interval the two span.  Where the two oracles agree this is the plain +-2 bar.
+iteration depends on rounding: on the oracle itself, perturbing B by one unit in the last place
+moves it by up to ~1.7 % (pinned on the CPU by test_oracle_pins.py::
+test_stopping_iteration_depends_on_rounding), and three builds of the oracle that differ only in
+rounding (FP64 as written; sums accumulated in long double; in addition, updates y + a x rounded
+once by fma) disagree by up to ~1.5 %.  FP64-mode GPU counts must lie in the interval the three
+builds span, widened on each side by max(2, 1 % of the count).  Double-word inner solves carry
+about 2^-48 rounding (32 times FP64's) and are checked against the same interval widened by 3 %
+(mixed-precision counts are reported rather than held to the FP64 bar).
 
 Residuals.  FP64 mode returns BMINRES_OK only if the FP64 true residual of every column is <= tol,
 and BMINRES_RESIDUAL_GAP if the recursive residual met tol but the true one did not; the latter is
@@ -17,21 +21,43 @@ from __future__ import annotations
 import numpy as np
 
 SLACK = 2
+REL_FP64 = 0.01
+REL_DW = 0.03
+BUILDS = ("fp64", "ext", "extfma")
+
+
+class OracleSet:
+    """The parity oracle's result and the stopping iterations of its three rounding builds."""
+
+    def __init__(self, ref, iters):
+        self.ref = ref
+        self.iters = dict(iters)
+
+    @property
+    def lo(self) -> int:
+        return min(self.iters.values())
+
+    @property
+    def hi(self) -> int:
+        return max(self.iters.values())
 
 
 def oracle_pair(oracle_mod, A, B, **kw):
-    """The parity oracle and its extended-accumulation build on the same inputs."""
+    """The parity oracle and the iteration counts of its rounding builds on the same inputs."""
     ref = oracle_mod.bminres(A, B, **kw)
-    ext = oracle_mod.bminres(A, B, variant="ext", **kw)
-    return ref, ext
+    its = {"fp64": ref.iters}
+    for v in BUILDS[1:]:
+        its[v] = oracle_mod.bminres(A, B, variant=v, **kw).iters
+    return ref, OracleSet(ref, its)
 
 
-def iter_bracket(ref, ext, slack: int = SLACK) -> tuple[int, int]:
-    return min(ref.iters, ext.iters) - slack, max(ref.iters, ext.iters) + slack
+def iter_bracket(ref, ext, rel: float = REL_FP64) -> tuple[int, int]:
+    w = max(SLACK, int(rel * ext.hi + 0.5))
+    return ext.lo - w, ext.hi + w
 
 
-def iters_ok(gpu_iters: int, ref, ext, slack: int = SLACK) -> bool:
-    lo, hi = iter_bracket(ref, ext, slack)
+def iters_ok(gpu_iters: int, ref, ext, rel: float = REL_FP64) -> bool:
+    lo, hi = iter_bracket(ref, ext, rel)
     return lo <= gpu_iters <= hi
 
 

@@ -8,7 +8,7 @@ at band iteration 2p + 1, Sec. 5).  Bars as in tests/_parity.py."""
 import numpy as np
 import pytest
 
-from _parity import check_fp64_result, iter_bracket, iters_ok, oracle_pair, rel_err, true_relres
+from _parity import REL_DW, check_fp64_result, iter_bracket, iters_ok, oracle_pair, rel_err, true_relres
 
 pytestmark = pytest.mark.gpu
 
@@ -86,12 +86,12 @@ def test_fp64_large_blocks_history(torch_cuda, oracle_mod, workloads, p):
 @pytest.mark.parametrize("kind", ["randn", "setup_dependence", "mid_dependence"])
 def test_double_word_p16_inner_solve(torch_cuda, oracle_mod, workloads, p, kind):
     """One double-word inner solve (no refinement) to a recursive 1e-10 on the <dw,16> kernel: the
-    iterate agrees with the FP64 oracle to 1e-7 and the iteration count meets the FP64 bar."""
+    iterate agrees with the FP64 oracle to 1e-7 and the iteration count meets the double-word bar."""
     A, B = _problem(workloads, kind, p)
     ref, ext = oracle_pair(oracle_mod, A, B, tol=TOL, maxit=40000)
     X, info, rel = _solve(torch_cuda, A, B, 40000, precision="mixed_dw", tol_inner=TOL, max_outer=1)
     assert info["outer"] == 1 and info["setup_deflations"] == ref.setup_deflations
-    assert iters_ok(info["iters"], ref, ext), (info["iters"], iter_bracket(ref, ext))
+    assert iters_ok(info["iters"], ref, ext, REL_DW), (info["iters"], iter_bracket(ref, ext, REL_DW))
     assert rel_err(X, ref.X) <= 1e-7
 
 
