@@ -61,32 +61,6 @@ __global__ void __launch_bounds__(AUX_NT) residual_kernel(int64_t n, int p, cons
   }
 }
 
-// Column ranges of the nonzeros of each chunk of WIN_CHUNK rows, by distance from the diagonal:
-// near (|col - row| <= WIN_NEAR), far below (col < row - WIN_NEAR) and far above (col > row + WIN_NEAR).
-// out[8c .. 8c+5] = near min, near max, below min, below max, above min, above max (min > max when
-// a class is empty); out[8c+6 .. 8c+7] = 0.  The persistent solve stages, for each block-product
-// tile, the row windows of the block vectors that these ranges span.
-constexpr int WIN_CHUNK = 32;
-constexpr int WIN_NEAR = 256;
-static __global__ void __launch_bounds__(AUX_NT) chunk_windows_kernel(int64_t n, const int32_t* __restrict__ rowptr,
-                                                                     const int32_t* __restrict__ colidx, int32_t* out) {
-  const int64_t c = (int64_t)blockIdx.x * AUX_NT + threadIdx.x;
-  if (c >= (n + WIN_CHUNK - 1) / WIN_CHUNK) return;
-  int v[6] = {0x7fffffff, -1, 0x7fffffff, -1, 0x7fffffff, -1};
-  const int64_t r1 = min(n, (c + 1) * WIN_CHUNK);
-  for (int64_t r = c * WIN_CHUNK; r < r1; ++r)
-    for (int32_t k = rowptr[r]; k < rowptr[r + 1]; ++k) {
-      const int col = colidx[k];
-      const int64_t d = (int64_t)col - r;
-      const int cls = d < -WIN_NEAR ? 1 : (d > WIN_NEAR ? 2 : 0);
-      v[2 * cls] = min(v[2 * cls], col);
-      v[2 * cls + 1] = max(v[2 * cls + 1], col);
-    }
-  int4* o = reinterpret_cast<int4*>(out) + 2 * c;
-  o[0] = make_int4(v[0], v[1], v[2], v[3]);
-  o[1] = make_int4(v[4], v[5], 0, 0);
-}
-
 // out[c] = sqrt(sum_b part[c][b]) for c < p (one block, fixed order).
 static __global__ void finish_norms_kernel(int p, int nparts, const double* part, double* out) {
   __shared__ double red[AUX_NT];

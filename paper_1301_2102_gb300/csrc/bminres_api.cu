@@ -52,7 +52,6 @@ struct bminres_handle_s {
   int32_t* rowptr = nullptr;
   int32_t* colidx = nullptr;
   double* vals = nullptr;
-  int32_t* chunks = nullptr;  // column ranges per 32-row chunk (block-product windows)
   float* vals32 = nullptr;   // FP32 copy of the values (MIXED)
   bmr::dw* vals_dw = nullptr; // double-word copy of the values (MIXED_DW)
   bmr::Ctl* ctl = nullptr;      // device
@@ -299,7 +298,6 @@ bminres_status persistent_solve(bminres_handle h, int p, V* Xout, double tol, in
   a.rowptr = h->rowptr;
   a.colidx = h->colidx;
   a.vals = vals;
-  a.chunks = h->chunks;
   a.F = (const V*)w.F;
   a.X = Xout;
   a.U = (V*)w.U;
@@ -563,9 +561,6 @@ bminres_status bminres_create(bminres_handle* out, int64_t n, int64_t nnz, const
   if (cudaMalloc(&h->rowptr, sizeof(int32_t) * (n + 1)) != cudaSuccess) return fail(BMINRES_ERR_OOM);
   if (cudaMalloc(&h->colidx, sizeof(int32_t) * std::max<int64_t>(nnz, 1)) != cudaSuccess) return fail(BMINRES_ERR_OOM);
   if (cudaMalloc(&h->vals, sizeof(double) * std::max<int64_t>(nnz, 1)) != cudaSuccess) return fail(BMINRES_ERR_OOM);
-  const int64_t nchunks = (n + bmr::WIN_CHUNK - 1) / bmr::WIN_CHUNK;
-  if (cudaMalloc(&h->chunks, sizeof(int32_t) * 8 * std::max<int64_t>(nchunks, 1)) != cudaSuccess)
-    return fail(BMINRES_ERR_OOM);
   if (o.precision == BMINRES_MIXED &&
       cudaMalloc(&h->vals32, sizeof(float) * std::max<int64_t>(nnz, 1)) != cudaSuccess)
     return fail(BMINRES_ERR_OOM);
@@ -582,11 +577,6 @@ bminres_status bminres_create(bminres_handle* out, int64_t n, int64_t nnz, const
     return fail(BMINRES_ERR_CUDA);
   if (nnz > 0 && cudaMemcpy(h->colidx, ci.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(BMINRES_ERR_CUDA);
-  if (nchunks > 0) {
-    bmr::chunk_windows_kernel<<<(int)((nchunks + bmr::AUX_NT - 1) / bmr::AUX_NT), bmr::AUX_NT>>>(n, h->rowptr, h->colidx,
-                                                                                               h->chunks);
-    if (cudaGetLastError() != cudaSuccess) return fail(BMINRES_ERR_CUDA);
-  }
   *out = h;
   bminres_status s = bminres_set_values(h, vals, nullptr);
   if (s != BMINRES_OK) {
@@ -625,7 +615,6 @@ void bminres_destroy(bminres_handle h) {
   if (h->rowptr) cudaFree(h->rowptr);
   if (h->colidx) cudaFree(h->colidx);
   if (h->vals) cudaFree(h->vals);
-  if (h->chunks) cudaFree(h->chunks);
   if (h->vals32) cudaFree(h->vals32);
   if (h->vals_dw) cudaFree(h->vals_dw);
   if (h->ctl) cudaFree(h->ctl);

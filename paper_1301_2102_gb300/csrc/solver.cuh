@@ -61,7 +61,6 @@ struct SolveArgs {
   const int32_t* rowptr;
   const int32_t* colidx;
   const V* vals;
-  const int32_t* chunks;  // column ranges of 32-row chunks (chunk_windows_kernel), or null
   const V* F;  // p vectors: initial block residual F0
   V* X;
   V* U;
@@ -106,9 +105,6 @@ struct __align__(16) Shared {
   unsigned long long tbar[NSTAGE_MAX];  // completion barriers of the staging buffers
   unsigned long long bar_epoch;         // grid barriers this block has passed (thread 0)
   int tq[TQMAX + 1];                // rowptr at the block-product tile boundaries of this block
-  // column ranges (near, far below, far above: min, max) of each block-product tile of this block,
-  // tabulated at set-up from the chunk table (p <= 16; larger blocks read the chunk table per tile)
-  int tw[PM <= 16 ? TQMAX : 1][6];
   int tq_n;                         // tiles tabulated (-1: too many, CSR read directly)
   int csr_nnz;                      // rowptr[n]
   // vectors staged by the current streaming pass: global address of row 0 and byte offset of
@@ -116,10 +112,6 @@ struct __align__(16) Shared {
   const char* cp_src[3 * PM + 8];
   unsigned cp_dst[3 * PM + 8];
   int cp_n, cp_pad;
-  // block-product tile in each staging buffer (written by the issuing warp before its arrival on the
-  // buffer's mbarrier): byte offset of the values and of the window region, slot stride (elements),
-  // then start and length (rows) of windows 0 (own rows and near columns), 1 (far below), 2 (far above)
-  int spw[NSTAGE_MAX][10];
   int terr, pad_t;                  // a staging wait ran out in this block
   int cycle, status, qstop, qstatus;
   int bench_next, n_ghost, deflations, setup_defl;
@@ -305,24 +297,15 @@ struct Tiles {
     return cap(nsl) >= NS * group(nsl) ? cap(nsl) / (NS * group(nsl)) * (NS * group(nsl)) : cap(nsl) / 32 * 32;
   }
   __host__ __device__ static constexpr size_t smem_bytes() { return SH + NSTAGE * STG; }
-  // block product: rows per tile and group width.  A tile's buffer holds its CSR segment (rowptr,
-  // colidx, values: up to 8 nonzeros per row on average) followed by the column windows of the p
-  // block vectors (at least the tile's own rows, sp_bytes).  The group width is the largest whose
-  // tile also leaves room, next to an average 7-nonzero segment, for two far windows of T rows and a
-  // near margin of 2 x 128 rows (a 3D 7-point stencil on a 128^3 grid: sp_want_bytes).
-  __host__ __device__ static constexpr size_t sp_csr_bytes(int t, int nnz_row) {
-    return ((size_t)(t + 4) * 4 + 15) / 16 * 16 + ((size_t)nnz_row * t * 4 + 15) / 16 * 16 +
-           (size_t)nnz_row * t * sizeof(V);
-  }
+  // block product: rows per tile and group width, with the tile's CSR segment staged beside the
+  // 2p vector slots (up to 8 nonzeros per row on average)
   __host__ __device__ static constexpr size_t sp_bytes(int t) {
-    return sp_csr_bytes(t, 8) + (size_t)PM * t * sizeof(V);
-  }
-  __host__ __device__ static constexpr size_t sp_want_bytes(int t) {
-    return sp_csr_bytes(t, 7) + (size_t)PM * (3 * t + 256 + 48 / sizeof(V)) * sizeof(V);
+    return ((size_t)2 * PM * t * sizeof(V) + (size_t)(t + 4) * 4 + 15) / 16 * 16 +
+           ((size_t)8 * t * 4 + 15) / 16 * 16 + (size_t)8 * t * sizeof(V);
   }
   __host__ __device__ static constexpr int sp_group() {
     int g = 16 / (int)sizeof(V);
-    while (g > 1 && (sp_bytes(NS * g) > STG || sp_want_bytes(NS * g) > STG)) g /= 2;
+    while (g > 1 && sp_bytes(NS * g) > STG) g /= 2;
     return g;
   }
   __host__ __device__ static constexpr int sp_rows() {
@@ -647,13 +630,9 @@ struct Engine {
   // W_k = A u_{j0+k}; w'_{j0} = W_0 - sum_{i<j0} h_{j0,i} u_i (into W slot 0); inner products
   // u_{j0+k} . w'_{j0}; removed-vector products; ||W_0||^2.  The control warp runs the QR step of
   // iteration qr_j (if > 0) meanwhile.
-  // Staged per tile by bulk copies: the tile's CSR segment (rowptr, colidx and values, copied in
-  // whole 16-byte units; entries outside the copied ranges are read directly) and up to three row
-  // windows of each block vector u_{j0} .. u_{j0+p-1}: the tile's own rows widened to its near
-  // columns, and the spans of its far-below and far-above columns, as far as they fit the buffer
-  // (for a 3D 7-point stencil: the +-1 and +-N neighbours and the two +-N^2 planes).  Columns outside
-  // every window are gathered from global memory.  The known-coefficient vectors u_{j0-p} ..
-  // u_{j0-1} are read row by row from global memory (coalesced).
+  // Staged per tile: u_{j0} .. u_{j0+p-1} (own rows; they also serve the gathers that fall in the
+  // tile), u_{j0-p} .. u_{j0-1}, and the tile's CSR segment: rowptr, colidx and values, copied in
+  // whole 16-byte units inside the arrays (entries outside the copied ranges are read directly).
 
   // rowptr at this block's block-product tile boundaries (the CSR structure is fixed per solve)
   __device__ void tabulate_csr_tiles() {
@@ -667,34 +646,7 @@ struct Engine {
       sh.tq_n = fit ? nt : -1;
       sh.csr_nnz = __ldg(a.rowptr + a.n);
     }
-    if constexpr (PM <= 16) {
-      if (fit && a.chunks)  // one warp per tile: the column ranges of the tile's chunks, reduced
-        for (int i = warp; i < nt; i += NT / 32) {
-          int v[6];
-          chunk_ranges(rb + (int64_t)i * T, (int)min((int64_t)T, nrows - (int64_t)i * T), v);
-          if (lane < 6) sh.tw[i][lane] = v[lane];
-        }
-    }
     __syncthreads();
-  }
-
-  // (one warp) min / max columns of the three classes over the chunks of rows [r0, r0 + rows)
-  __device__ __forceinline__ void chunk_ranges(int64_t r0, int rows, int (&v)[6]) const {
-    v[0] = v[2] = v[4] = 0x7fffffff;
-    v[1] = v[3] = v[5] = -1;
-    const int64_t c0 = r0 / 32, nc = (rows + 31) / 32;
-    if (lane < nc) {
-      const int4 q0 = __ldg(reinterpret_cast<const int4*>(a.chunks) + 2 * (c0 + lane));
-      const int4 q1 = __ldg(reinterpret_cast<const int4*>(a.chunks) + 2 * (c0 + lane) + 1);
-      v[0] = q0.x; v[1] = q0.y; v[2] = q0.z; v[3] = q0.w; v[4] = q1.x; v[5] = q1.y;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int k = 0; k < 6; k += 2) {
-        v[k] = min(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
-        v[k + 1] = max(v[k + 1], __shfl_xor_sync(0xffffffffu, v[k + 1], o));
-      }
   }
 
   struct CsrTile {
@@ -718,59 +670,6 @@ struct Engine {
     return c;
   }
 
-  // (warp 1, all lanes) windows of block-product tile rows [r0, r0 + rows) whose p slots fit `avail`
-  // rows each: writes w[2..7] (start, length of windows 0..2) and returns the slot stride.  Window 0
-  // always holds the own rows; then the far-below and far-above spans (each if it is at most 2T rows),
-  // then the near margin.  Starts and lengths are whole 16-byte units, inside [0, ld).
-  __device__ int sp_windows(int64_t r0, int rows, int avail, int* w) const {
-    constexpr int T = TL::sp_rows();
-    constexpr int AL = 16 / (int)sizeof(V);  // elements per 16 bytes
-    int v[6] = {0x7fffffff, -1, 0x7fffffff, -1, 0x7fffffff, -1};
-    if (a.chunks) {
-      const int ti = (int)((r0 - rb) / T);
-      if (PM <= 16 && sh.tq_n >= 0) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) v[k] = sh.tw[PM <= 16 ? ti : 0][k];
-      } else {
-        chunk_ranges(r0, rows, v);
-      }
-    }
-    const int64_t ld = a.ld;
-    auto lo = [&](int64_t x) { return max((int64_t)0, x / AL * AL); };
-    auto hi = [&](int64_t x) { return min(ld, (x + AL - 1) / AL * AL); };
-    int64_t a0 = r0, e0 = hi(r0 + rows);
-    int used = (int)(e0 - a0);
-    int64_t wa[2] = {0, 0}, wn[2] = {0, 0};
-#pragma unroll
-    for (int f = 0; f < 2; ++f) {
-      const int mn = v[2 + 2 * f], mx = v[3 + 2 * f];
-      if (mn <= mx) {
-        const int64_t s0 = lo(mn), s1 = hi((int64_t)mx + 1);
-        const int len = (int)(s1 - s0);
-        if (len <= 2 * T && used + len <= avail) {
-          wa[f] = s0;
-          wn[f] = len;
-          used += len;
-        }
-      }
-    }
-    if (v[0] <= v[1]) {
-      const int64_t n0a = lo(min((int64_t)v[0], r0)), n0e = hi(max((int64_t)v[1] + 1, r0 + rows));
-      if (used + (int)((n0e - n0a) - (e0 - a0)) <= avail) {
-        used += (int)((n0e - n0a) - (e0 - a0));
-        a0 = n0a;
-        e0 = n0e;
-      }
-    }
-    w[2] = (int)a0;
-    w[3] = (int)(e0 - a0);
-    w[4] = (int)wa[0];
-    w[5] = (int)wn[0];
-    w[6] = (int)wa[1];
-    w[7] = (int)wn[1];
-    return used;
-  }
-
   __device__ bool pass_spmm(int j0, int qr_j, int qr_l) {
     R acc[LY::SP_N];  // written after the streaming loop
     int ng = 0;
@@ -783,8 +682,10 @@ struct Engine {
       for (int k = 0; k < LY::SP_N; ++k) acc[k] = R{};
     } else {
       constexpr int T = TL::sp_rows(), G = TL::sp_group();
-      constexpr size_t OCI = ((size_t)(T + 4) * 4 + 15) / 16 * 16;  // colidx; rowptr at 0
-      static_assert(TL::sp_bytes(T) <= TL::STG, "block-product tile");
+      constexpr size_t OUK = (size_t)PM * T * sizeof(V), ORP = 2 * OUK;
+      constexpr size_t OCI = ORP + ((size_t)(T + 4) * 4 + 15) / 16 * 16;
+      constexpr size_t OCV = OCI + ((size_t)8 * T * 4 + 15) / 16 * 16;
+      static_assert(OCV + (size_t)8 * T * sizeof(V) <= TL::STG, "block-product tile");
       const bool csr_al = ((reinterpret_cast<uintptr_t>(a.rowptr) | reinterpret_cast<uintptr_t>(a.colidx) |
                             reinterpret_cast<uintptr_t>(a.vals)) & 15u) == 0;
       // coefficients (negated), scales and slot addresses of u_{j0+k}: registers for p <= 8, computed
@@ -825,72 +726,34 @@ struct Engine {
       for (int k = 0; k < PM; ++k) adot[k] = R{};
 #pragma unroll
       for (int g = 0; g < NBMAX; ++g) agh[g] = R{};
+      if (warp == 1) {  // copy list: u_{j0+k} into slot k, u_{j0-p+k} into slot PM + k
+        const int n = has_known ? 2 * p : p;
+        for (int c = lane; c < n; c += 32)
+          cp_put(c, c < p ? uslot(j0 + c) : uslot(j0 - p + (c - p)), c < p ? c : PM + (c - p), T);
+        if (lane == 0) sh.cp_n = n;
+        __syncwarp();
+      }
       auto issue = [&](int sb, int64_t r0, int rows) __attribute__((always_inline)) {
         const CsrTile c = csr_tile((int)((r0 - rb) / T), r0, rows, csr_al);
         const unsigned bq = c.ok ? (unsigned)(c.qb - c.qa) : 0u;
         const unsigned brp = c.ok ? (unsigned)c.nrp * 4u : 0u;
-        const unsigned ocv = (unsigned)OCI + (bq * 4u + 15u) / 16u * 16u;
-        const unsigned ow = ocv + (bq * (unsigned)sizeof(V) + 15u) / 16u * 16u;
-        const int avail = (int)((TL::STG - ow) / ((size_t)p * sizeof(V))) / (16 / (int)sizeof(V)) *
-                          (16 / (int)sizeof(V));
-        int w[10];
-        const int rs = sp_windows(r0, rows, avail, w);
-        w[0] = (int)ow;
-        w[1] = rs;
-        w[8] = (int)ocv;
-        w[9] = 0;
+        cp_issue(sb, r0, rows, brp + bq * (4u + (unsigned)sizeof(V)));
         unsigned long long* bar = &sh.tbar[sb];
         char* d = reinterpret_cast<char*>(stage(sb));
-        if (lane == 0) {
-#pragma unroll
-          for (int q = 0; q < 10; ++q) sh.spw[sb][q] = w[q];
-          mbar_arrive_expect_tx(bar, brp + bq * (4u + (unsigned)sizeof(V)) + (unsigned)((size_t)p * rs * sizeof(V)));
-        }
-        __syncwarp();
-        if (lane == 0 && brp) bulk_g2s(d, a.rowptr + r0, brp, bar);
+        if (lane == 0 && brp) bulk_g2s(d + ORP, a.rowptr + r0, brp, bar);
         if (lane == 1 && bq) bulk_g2s(d + OCI, a.colidx + c.qa, bq * 4u, bar);
-        if (lane == 2 && bq) bulk_g2s(d + ocv, a.vals + c.qa, bq * (unsigned)sizeof(V), bar);
-        // p slots x 3 windows, one copy each (empty windows skipped)
-        for (int q = lane; q < 3 * p; q += 32) {
-          const int k = q / 3, wi = q - 3 * k;
-          const int len = w[3 + 2 * wi];
-          if (len > 0) {
-            const int off = (wi == 0) ? 0 : (wi == 1 ? w[3] : w[3] + w[5]);
-            bulk_g2s(d + ow + ((size_t)k * rs + off) * sizeof(V), uk(k) + w[2 + 2 * wi],
-                     (unsigned)((size_t)len * sizeof(V)), bar);
-          }
-        }
+        if (lane == 2 && bq) bulk_g2s(d + OCV, a.vals + c.qa, bq * (unsigned)sizeof(V), bar);
       };
       auto body = [&](auto gt, const V* tl, int o, int64_t r, int rows) __attribute__((always_inline)) {
         constexpr int GG = decltype(gt)::value;
         constexpr int QC = 8;  // nonzeros of every row of the group fetched together
         constexpr int QH = (PM * sizeof(V) <= 32) ? QC : (PM * sizeof(V) <= 64 ? QC / 2 : 1);  // gathers in flight
         const int64_t r0 = r - o;  // first row of the tile
-        const int sb = (tl == stage(0)) ? 0 : 1;
-        const int* wd = sh.spw[sb];
-        const int rs = wd[1], wa0 = wd[2], wn0 = wd[3], wa1 = wd[4], wn1 = wd[5], wa2 = wd[6], wn2 = wd[7];
         const CsrTile c = csr_tile((int)((r0 - rb) / T), r0, rows, csr_al);
         const char* tb = reinterpret_cast<const char*>(tl);
-        const int32_t* rps = reinterpret_cast<const int32_t*>(tb);
+        const int32_t* rps = reinterpret_cast<const int32_t*>(tb + ORP);
         const int32_t* cis = reinterpret_cast<const int32_t*>(tb + OCI);
-        const V* cvs = reinterpret_cast<const V*>(tb + wd[8]);
-        const V* win = reinterpret_cast<const V*>(tb + wd[0]);
-        // known-coefficient vectors u_{j0-p} .. u_{j0-1} of these rows, loaded first so that their
-        // latency overlaps the product (p <= 8; larger blocks load them where they are used)
-        constexpr bool KPRE = PM <= 8;
-        A kv[KPRE ? PM : 1][GG];
-        auto kload = [&](int k, A (&x)[GG]) __attribute__((always_inline)) {
-          int ks = s0 + p + k;  // slot of u_{j0-p+k}: (s0 - p + k) mod 2p
-          if (ks >= 2 * p) ks -= 2 * p;
-          vld<GG>(a.U + (int64_t)ks * a.ld + r, x);
-        };
-        if constexpr (KPRE) {
-          if (has_known) {
-#pragma unroll
-            for (int k = 0; k < PM; ++k)
-              if (k < p) kload(k, kv[k]);
-          }
-        }
+        const V* cvs = reinterpret_cast<const V*>(tb + OCV);
         int32_t kb[GG + 1];
 #pragma unroll
         for (int e = 0; e <= GG; ++e) {
@@ -905,9 +768,7 @@ struct Engine {
         int32_t mx = 0;
 #pragma unroll
         for (int e = 0; e < GG; ++e) mx = max(mx, kb[e + 1] - kb[e]);
-        // longest row among the lanes taking this path together: slots beyond it are skipped
-        const int32_t mxw = __reduce_max_sync(__activemask(), (unsigned)mx);
-        for (int32_t q0 = 0; q0 < mxw; q0 += QC) {
+        for (int32_t q0 = 0; q0 < mx; q0 += QC) {
           int32_t ci[GG][QC];
           A cv[GG][QC];
 #pragma unroll
@@ -927,39 +788,36 @@ struct Engine {
                 }
               }
             }
-          // each nonzero's p values come from a staged window (shared memory) or, for a column
-          // outside every window, from global memory (predicated loads, a group issued before any
-          // is used); the products are summed in CSR order whatever the source
+          // columns whose rows lie in the tile come from the staged copy; the others are gathered
+          // from global memory by predicated loads, all issued before any is used (one round trip
+          // per row of the group)
 #pragma unroll
           for (int e = 0; e < GG; ++e) {
+            bool out[QC];
+#pragma unroll
+            for (int qq = 0; qq < QC; ++qq) {
+              const int64_t col = ci[e][qq];
+              const uint64_t ct = (uint64_t)(col - r0);
+              out[qq] = ci[e][qq] >= 0 && ct >= (uint64_t)rows;
+              if (ci[e][qq] >= 0 && ct < (uint64_t)rows) {
+#pragma unroll
+                for (int k = 0; k < PM; ++k)
+                  if (k < p) wk[k][e] = madd(cv[e][qq], tl[k * T + ct], wk[k][e]);
+              }
+            }
 #pragma unroll
             for (int h = 0; h < QC; h += QH) {
-              if (q0 + h < mxw) {
-                A gv[QH][PM];
+              A gv[QH][PM];
 #pragma unroll
-                for (int qq = 0; qq < QH; ++qq) {
-                  const int col = ci[e][h + qq];
-                  const unsigned d0 = (unsigned)(col - wa0), d1 = (unsigned)(col - wa1),
-                                 d2 = (unsigned)(col - wa2);
-                  const int off = col < 0 ? -2
-                                  : d0 < (unsigned)wn0 ? (int)d0
-                                  : d1 < (unsigned)wn1 ? wn0 + (int)d1
-                                  : d2 < (unsigned)wn2 ? wn0 + wn1 + (int)d2
-                                                       : -1;
+              for (int qq = 0; qq < QH; ++qq)
 #pragma unroll
-                  for (int k = 0; k < PM; ++k)
-                    gv[qq][k] = (k < p && off >= 0)    ? (A)win[k * rs + (off >= 0 ? off : 0)]
-                                : (k < p && off == -1) ? (A)uk(k)[off == -1 ? col : 0]
-                                                       : (A)0;
-                }
+                for (int k = 0; k < PM; ++k)
+                  gv[qq][k] = (out[h + qq] && k < p) ? (A)uk(k)[out[h + qq] ? ci[e][h + qq] : 0] : (A)0;
 #pragma unroll
-                for (int qq = 0; qq < QH; ++qq)
-                  if (q0 + h + qq < mxw) {
+              for (int qq = 0; qq < QH; ++qq)
 #pragma unroll
-                    for (int k = 0; k < PM; ++k)
-                      if (k < p) wk[k][e] = madd(cv[e][h + qq], gv[qq][k], wk[k][e]);
-                  }
-              }
+                for (int k = 0; k < PM; ++k)
+                  if (k < p) wk[k][e] = madd(cv[e][h + qq], gv[qq][k], wk[k][e]);
             }
           }
         }
@@ -972,26 +830,21 @@ struct Engine {
         }
 #pragma unroll
         for (int e = 0; e < GG; ++e) wp[e] = wk[0][e];
+        const V* sp = tl + o;
         if (has_known) {
 #pragma unroll
           for (int k = 0; k < PM; ++k)
             if (k < p) {
-              if constexpr (KPRE) {
-#pragma unroll
-                for (int e = 0; e < GG; ++e) x[e] = kv[k][e];
-              } else {
-                kload(k, x);
-              }
+              sld<GG>(sp + (PM + k) * T, x);
               const A ck = cAk(k);
 #pragma unroll
               for (int e = 0; e < GG; ++e) wp[e] = madd(ck, x[e], wp[e]);
             }
         }
-        const V* sp = win + (r0 - wa0) + o;  // own rows of the window
 #pragma unroll
         for (int k = 0; k < PM; ++k)
           if (k < p) {
-            sld<GG>(sp + k * rs, x);
+            sld<GG>(sp + k * T, x);
 #pragma unroll
             for (int e = 0; e < GG; ++e) dot_add(adot[k], x[e], wp[e]);
           }
