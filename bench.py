@@ -11,7 +11,7 @@ One step = one complete solve from X0 = 0 until the FP64 TRUE relative residual 
                 residual meets tol (the default headline: on this workload plain FP64 stops when its
                 recursive residual meets tol with a true residual near 7e-8, which misses the metric)
   mixed_dw      double-word (FP32 pair) inner solves in the same refinement loop (default second)
-  mixed         FP32 inner solves (the benchmark spec's mixed form; does not converge at 128^3)
+  mixed         FP32 inner solves in the same loop (does not converge at 128^3)
   fp64          the plain method, stopped by the recursive residual (reported with its true residual)
 
 Each timed step calls the public C ABI with B and X in pinned host memory: `value` is the CUDA-event
@@ -113,10 +113,10 @@ def algorithmic(n: int, nnz: int, p: int, nb: int, s: int):
 
 
 # DRAM bytes of bminres_solve_kernel<double,8> on this workload from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum over launches of 160 and 320 band iterations), per band iteration and for the
-# set-up.  None: the kernel has changed since the counters were taken.
-TRAFFIC_PER_ITER_F64 = None
-TRAFFIC_SETUP_F64 = None
+# dram__bytes_write.sum of launches of 160 and 320 band iterations: 91.002 GB and 180.268 GB), per band
+# iteration and for the set-up of one launch.  None: the kernel has changed since the counters were taken.
+TRAFFIC_PER_ITER_F64 = 557.9e6
+TRAFFIC_SETUP_F64 = 1.73e9
 
 
 def passes_report(info, n, nnz, p, s, sx, hbm):

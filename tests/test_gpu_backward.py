@@ -1,6 +1,6 @@
 """The adjoint of the block solve on the GPU (bminres_backward and the autograd Function):
 parity with the oracle-based adjoint, and central finite differences of GPU forward solves
-(spec bar: 1e-5 relative), on a small saddle-point system of the config-4 family."""
+(bar: 1e-5 relative), on a small saddle-point system of the config-4 family."""
 import numpy as np
 import pytest
 

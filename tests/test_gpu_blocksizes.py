@@ -107,7 +107,7 @@ def test_double_word_p16_refined_reaches_tol(torch_cuda, oracle_mod, workloads, 
 @pytest.mark.parametrize("p", [8, 16])
 @pytest.mark.parametrize("kind", ["randn", "setup_dependence"])
 def test_fp32_inner_solves_refined(torch_cuda, oracle_mod, workloads, p, kind):
-    """The benchmark spec's mixed form on the <float,8> and <float,16> kernels (the ones the mixed
+    """The FP32-inner mixed form on the <float,8> and <float,16> kernels (the ones the mixed
     benchmark mode times): FP32 vectors, block product and orthogonalisation inside FP64 iterative
     refinement reach an FP64 true residual <= tol; the error against the FP64 oracle is stated
     (bounded by the conditioning times tol: 1e-6 here)."""

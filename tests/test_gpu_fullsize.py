@@ -54,3 +54,37 @@ def test_double_word_first_iterations_at_full_size(torch_cuda, case):
     assert info["iters"] == K and info["setup_deflations"] == 2
     X = X.cpu().numpy()
     assert np.linalg.norm(X - ref.X) <= 1e-8 * np.linalg.norm(ref.X)
+
+
+@pytest.mark.parametrize("cfg", ["c3_128cube_p16", "c5_192cube_p32"])
+def test_large_block_first_cycles_at_full_size(torch_cuda, oracle_mod, workloads, cfg):
+    """The configurations with large blocks, at full size: 128^3 with p = 16 and 192^3 (sigma at 5 %)
+    with p = 32 N(0,1) right-hand sides, the first three (p = 16) or two (p = 32) cycles against the
+    oracle (its all-core build: the same steps, inner products summed in fixed chunks), FP64: recursive
+    residual history within 1e-10 of ||f0||, iterate within 1e-10; and the FP32 inner solve of the
+    mixed form over the same iterations within 1e-5."""
+    from paper_1301_2102_gb300 import Solver
+
+    if cfg == "c3_128cube_p16":
+        A, B = workloads.config_c3(16)
+        p, k = 16, 48
+    else:
+        A, B = workloads.config_c5()
+        p, k = 32, 64
+    ref = oracle_mod.bminres(A, B, tol=1e-14, maxit=k, hist=k, variant="omp")
+    Bd = torch_cuda.from_numpy(B).cuda()
+    with Solver(A) as s:
+        s.set_history(k)
+        X, info, rel = s.solve(Bd, tol=1e-14, maxit=k)
+        H = s.history(p)
+    assert info["iters"] == k == ref.iters and info["grid_blocks"] == 152
+    assert np.abs(H - ref.rho).max() <= 1e-10 * ref.f0norm.max()
+    assert np.linalg.norm(X.cpu().numpy() - ref.X) <= 1e-10 * np.linalg.norm(ref.X)
+    del X
+    with Solver(A, precision="mixed", tol_inner=1e-14, max_outer=1) as s:
+        s.set_history(k)
+        X, info, rel = s.solve(Bd, tol=1e-14, maxit=k)
+        H = s.history(p)
+    assert info["iters"] == k
+    assert np.abs(H - ref.rho).max() <= 1e-5 * ref.f0norm.max()
+    assert np.linalg.norm(X.cpu().numpy() - ref.X) <= 1e-5 * np.linalg.norm(ref.X)

@@ -430,7 +430,7 @@ def test_removed_vector_retention_breaks_the_residual_recursion(oracle_mod, work
 
 
 # ---------------------------------------------------------------------------------------------
-# P13: the adjoint of the block solve (spec extension, not in the paper)
+# P13: the adjoint of the block solve (an extension, not in the paper)
 # ---------------------------------------------------------------------------------------------
 
 def _symmetric_pairs(A):
