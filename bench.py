@@ -115,8 +115,8 @@ def algorithmic(n: int, nnz: int, p: int, nb: int, s: int):
 # DRAM bytes of bminres_solve_kernel<double,8> on this workload from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum of launches of 160 and 320 band iterations: 91.002 GB and 180.268 GB), per band
 # iteration and for the set-up of one launch.  None: the kernel has changed since the counters were taken.
-TRAFFIC_PER_ITER_F64 = 557.9e6
-TRAFFIC_SETUP_F64 = 1.73e9
+TRAFFIC_PER_ITER_F64 = None
+TRAFFIC_SETUP_F64 = None
 
 
 def passes_report(info, n, nnz, p, s, sx, hbm):
@@ -405,8 +405,12 @@ def run_ours(args):
                     "peak_source": hbm_src}
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["kernel"] = KERNEL[head]
-        roof["traffic"] = (TRAFFIC_SETUP_F64 * info["outer"] + TRAFFIC_PER_ITER_F64 * it
+        # per launch of the persistent kernel (one launch per refinement step), like `achieved`
+        launches = max(info["outer"], 1)
+        roof["traffic"] = (TRAFFIC_SETUP_F64 + TRAFFIC_PER_ITER_F64 * it / launches
                            if head in ("fp64", "fp64_refined") and TRAFFIC_PER_ITER_F64 else None)
+        roof["kernel_launches"] = launches
+        roof["algorithmic_bytes_per_launch"] = by * it / launches
         roof["hbm_gbs_bmin"] = by * it / ks / 1e9
         roof["hbm_frac_bmin"] = roof["hbm_gbs_bmin"] / hbm
         roof["bmin_bytes_per_iter"] = by

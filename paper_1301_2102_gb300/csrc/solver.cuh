@@ -814,10 +814,18 @@ struct Engine {
                 for (int k = 0; k < PM; ++k)
                   gv[qq][k] = (out[h + qq] && k < p) ? (A)uk(k)[out[h + qq] ? ci[e][h + qq] : 0] : (A)0;
 #pragma unroll
-              for (int qq = 0; qq < QH; ++qq)
+              for (int qq = 0; qq < QH; ++qq) {
+                // FP64 and double-word: a slot that no lane of the warp gathers (its column lies in
+                // the tile for every lane, or it is padding) would add only zeros; the warp skips it
+                // (for a stencil the slots are uniform over the 32 consecutive rows of a warp).  FP32
+                // keeps the unconditional form, which measured faster for it
+                if constexpr (!std::is_same<V, float>::value) {
+                  if (!__any_sync(__activemask(), out[h + qq])) continue;
+                }
 #pragma unroll
                 for (int k = 0; k < PM; ++k)
                   if (k < p) wk[k][e] = madd(cv[e][h + qq], gv[qq][k], wk[k][e]);
+              }
             }
           }
         }
