@@ -56,7 +56,7 @@ MAXIT = 4_000_000
 # (FP64 inner solves in FP64 refinement, two restarts to an inner 1e-6, measured on GB300; the oracle
 # follows the same iteration within the parity bar).  Used to scale the reference arm's sampled
 # oracle time per band iteration to a full solve; the repo arm uses its own measured count.
-REF_ITERS_128 = 1_556_125
+REF_ITERS_128 = 1_555_397
 REF_OUTER_128 = 2
 
 
@@ -113,10 +113,10 @@ def algorithmic(n: int, nnz: int, p: int, nb: int, s: int):
 
 
 # DRAM bytes of bminres_solve_kernel<double,8> on this workload from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum of launches of 160 and 320 band iterations: 91.002 GB and 180.268 GB), per band
+# dram__bytes_write.sum of launches of 160 and 320 band iterations: 90.971 GB and 180.217 GB), per band
 # iteration and for the set-up of one launch.  None: the kernel has changed since the counters were taken.
-TRAFFIC_PER_ITER_F64 = None
-TRAFFIC_SETUP_F64 = None
+TRAFFIC_PER_ITER_F64 = 557.8e6
+TRAFFIC_SETUP_F64 = 1.73e9
 
 
 def passes_report(info, n, nnz, p, s, sx, hbm):
