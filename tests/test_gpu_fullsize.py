@@ -88,3 +88,33 @@ def test_large_block_first_cycles_at_full_size(torch_cuda, oracle_mod, workloads
     assert info["iters"] == k
     assert np.abs(H - ref.rho).max() <= 1e-5 * ref.f0norm.max()
     assert np.linalg.norm(X.cpu().numpy() - ref.X) <= 1e-5 * np.linalg.norm(ref.X)
+
+
+def test_c5_adjoint_first_cycles_and_sampled_gradient(torch_cuda, oracle_mod, workloads):
+    """The adjoint of the 192^3, p = 32 configuration at full size, for L = sum(X^2) (G = 2X), with
+    forward and adjoint solves both capped at two cycles: the adjoint solve dB = A^{-1} G equals the
+    oracle's solve of the same right-hand side (its all-core build) to 1e-10, and the sampled outer
+    product dA_k = -sum_c dB[row_k, c] X[col_k, c] equals the same sum taken on the host from the
+    GPU's dB and X, at 4096 random stored entries of the 49 million."""
+    from paper_1301_2102_gb300 import Solver
+
+    A, B = workloads.config_c5()
+    k = 64
+    with Solver(A) as s:
+        X, info, rel = s.solve(torch_cuda.from_numpy(B).cuda(), tol=1e-14, maxit=k)
+        assert info["iters"] == k
+        G = (2.0 * X).contiguous()
+        dB, dA, binfo = s.backward(G, X, tol=1e-14, maxit=k)
+        assert binfo["iters"] == k
+        Gh, Xh, dBh = G.cpu().numpy(), X.cpu().numpy(), dB.cpu().numpy()
+        rng = np.random.default_rng(3)
+        picks = rng.choice(A.nnz, 4096, replace=False)
+        dAh = dA[torch_cuda.from_numpy(picks).cuda()].cpu().numpy()
+    del X, G, dB, dA
+    ref = oracle_mod.bminres(A, Gh, tol=1e-14, maxit=k, variant="omp")
+    assert ref.iters == k
+    assert np.linalg.norm(dBh - ref.X) <= 1e-10 * np.linalg.norm(ref.X)
+    rows = np.searchsorted(A.rowptr, picks, side="right") - 1
+    cols = A.colidx[picks]
+    want = -np.einsum("ij,ij->i", dBh[rows], Xh[cols])
+    assert np.abs(dAh - want).max() <= 1e-12 * np.abs(want).max()
